@@ -1,0 +1,267 @@
+/*
+ * mp.h -- C ABI of the GB300 multipath Metropolis library for the classical
+ * O(3) Heisenberg model (Rakic, Radosevic, Mali, Stricevic, Petric,
+ * "Multipath Metropolis Simulation of Classical Heisenberg Model").
+ *
+ * The method (Sec. 2.2): many mutually independent Metropolis random walks
+ * ("simulation paths") of one lattice at one temperature, each started from a
+ * random state, thermalised by lattice sweeps and then measured; the per-path
+ * outputs {M^x, M^y, M^z, H} (per lattice site) are averaged over paths,
+ * Eq. (MCAV), into ensemble estimates with standard errors.
+ *
+ * Model (Sec. 2.1): H = -(J/2) sum_n sum_lambda S_n . S_{n+lambda} - h sum_n S^z_n,
+ * Eq. (1) plus a Zeeman term (h = 0 is the paper's model), unit spins of Eq. (2),
+ * on a periodic simple-cubic lattice of N = L^3 sites (L even, 2 <= L <= 24 for
+ * the shared-memory kernels) or an open chain of N = L spins.
+ *
+ * Conventions shared by every call:
+ *   - Every function returns an int status (MP_OK or a negative MP_E* code),
+ *     except mp_destroy and the string helpers.  On error nothing observable
+ *     changes except the handle's last-error text (mp_last_error).
+ *   - "host" pointers are ordinary CPU memory owned by the caller; "device"
+ *     pointers are CUDA global memory on the handle's device.
+ *   - A handle is not thread-safe: use one handle per host thread.
+ *   - All GPU work of a handle is issued on its stream (mp_config.stream);
+ *     calls that return host data synchronise that stream first.
+ *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = (seed low 32
+ *     bits, seed high 32 bits), counter = (site, sweep, path id within its
+ *     system, tag | system index << 8), tag 0 = update, 1 = initial state.
+ *     Results are therefore a pure function of (config, seed), independent of
+ *     launch shape and GPU.
+ */
+#ifndef MP_H
+#define MP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status -- */
+#define MP_OK 0
+#define MP_EINVAL (-1)     /* bad argument (see each call) */
+#define MP_ENOMEM (-2)     /* the allocator returned NULL */
+#define MP_ECUDA (-3)      /* a CUDA runtime call failed; see mp_last_error */
+#define MP_ESTATE (-4)     /* call out of order, e.g. estimates before a run */
+#define MP_ECANCELED (-5)  /* mp_cancel stopped the run before it finished */
+#define MP_ETIMEOUT (-6)   /* reserved: the library has no unbounded waits */
+
+/* ---------------------------------------------------------------- enums --- */
+#define MP_LATTICE_SC 0    /* periodic simple cubic, N = L^3, L even */
+#define MP_LATTICE_CHAIN 1 /* open chain, N = L >= 2 */
+
+#define MP_FP32 0 /* FP32 spins, dE and Boltzmann factor; FP64 accumulators */
+#define MP_FP64 1 /* FP64 throughout (the plain FP64 GPU form) */
+
+#define MP_INIT_SPHERE 0  /* uniform on the sphere (Sec. 4, "uniform state") */
+#define MP_INIT_ANGLES 1  /* theta, phi each uniform (Sec. 2.2 "both angles") */
+#define MP_INIT_ORDERED 2 /* all spins along +z (Sec. 5, ordered start) */
+
+#define MP_FLAG_GRAPH 1u      /* capture each run in a CUDA graph and replay it */
+#define MP_FLAG_KEEP_SPINS 2u /* keep every path's final spins (mp_spins) */
+
+/* ------------------------------------------------------------- records ---
+ * Per-path record: MP_NREC doubles per path.  Fields 0..12 are means over the
+ * path's n_meas measurement sweeps of per-site observables of the state after
+ * each sweep: e = H/N (energy per site, Eq. 1 plus Zeeman term) and
+ * m = (1/N) sum_n S_n (Sec. 2.2).  Fields 13..16 are the state after the last
+ * sweep (the paper's per-path output {M^x, M^y, M^z, H}).  n_meas = 1 gives
+ * exactly the paper's single final-state output. */
+enum {
+  MP_R_E = 0,   /* <e> */
+  MP_R_E2,      /* <e^2> */
+  MP_R_M,       /* <|m|> */
+  MP_R_M2,      /* <|m|^2> */
+  MP_R_M4,      /* <|m|^4> */
+  MP_R_MX,      /* <m_x> */
+  MP_R_MY,      /* <m_y> */
+  MP_R_MZ,      /* <m_z> */
+  MP_R_MZ2,     /* <m_z^2> */
+  MP_R_AMZ,     /* <|m_z|> */
+  MP_R_EM,      /* <e |m|> */
+  MP_R_EMZ,     /* <e m_z> */
+  MP_R_MMZ,     /* <|m| m_z> */
+  MP_R_FMX,     /* final m_x */
+  MP_R_FMY,     /* final m_y */
+  MP_R_FMZ,     /* final m_z */
+  MP_R_FE,      /* final e */
+  MP_R_ACC,     /* accepted / attempted moves over all sweeps */
+  MP_R_NORM,    /* max over sites of | |S| - 1 | in the final state */
+  MP_R_SPARE,
+  MP_NREC
+};
+
+/* ----------------------------------------------------------- estimates ---
+ * Ensemble estimates of one system, all doubles.  <A> is the mean over paths
+ * of the per-path means, Eq. (MCAV); *_se is its standard error
+ * (sample standard deviation over paths / sqrt(paths)).
+ *   chi      = (N/T) (<|m|^2> - <|m|>^2)                     Eq. (cv), left
+ *   cv       = (N/T^2) (<e^2> - <e>^2)                       Eq. (cv), right
+ *   binder   = 1 - <|m|^4> / (3 <|m|^2>^2)                   Eq. (kum)
+ *   dX_dbeta = -N (<X e> - <X><e>)       (fluctuation formula, X in {e,|m|,m_z})
+ *   dX_dh    = beta N (<X m_z> - <X><m_z>)
+ *   cv_m     = se(<|m|>) / <|m|>                             Eq. (eq:cv)
+ *   r_*      = 1 - ||R||^2 / ((P-1) sigma^2) of the normal Q-Q line fit of the
+ *              per-path values, plotting positions (i - 1/2)/P,
+ *              Eq. (dist-coefficient); NaN when P < 3 or P > MP_R_MAX_PATHS.
+ * SEs of derived quantities are delete-one jackknife over paths. */
+#define MP_R_MAX_PATHS 16384
+
+typedef struct {
+  double n_paths, N, T, n_meas;
+  double e, e_se, e2, e2_se;
+  double m, m_se, m2, m2_se, m4, m4_se;
+  double mx, mx_se, my, my_se, mz, mz_se;
+  double mz2, mz2_se, amz, amz_se;
+  double acc, acc_se;
+  double chi, chi_se, cv, cv_se, binder, binder_se;
+  double de_dbeta, de_dbeta_se, dm_dbeta, dm_dbeta_se, dmz_dbeta, dmz_dbeta_se;
+  double de_dh, de_dh_se, dm_dh, dm_dh_se, dmz_dh, dmz_dh_se;
+  double cv_m;
+  double r_e, r_m, r_mx, r_my, r_mz, r_amz;
+  double attempts; /* N x paths x (n_therm + n_meas) */
+  double norm_max; /* max over paths of MP_R_NORM */
+  double reserved[11];
+} mp_estimates_t; /* 64 doubles */
+
+#define MP_NEST 64
+
+/* --------------------------------------------------------------- config -- */
+typedef struct {
+  int32_t lattice; /* MP_LATTICE_* */
+  int32_t L;       /* linear size (SC) or number of spins (chain) */
+  double T;        /* temperature, k_B = 1 (Sec. 2.1 fixes J = 1 as the scale) */
+  double J;        /* exchange; J > 0 ferro, J < 0 antiferro (Sec. 2.1) */
+  double h;        /* field along +z (not in the paper; 0 reproduces it) */
+  int64_t n_paths; /* independent paths of this system, >= 1 */
+} mp_system;
+
+/* Device-memory allocator hooks.  alloc must return device memory of at least
+ * `bytes` bytes aligned to 256 bytes, or NULL; free releases it.  Both are
+ * called only from mp_create_ex / mp_destroy on the calling thread.  When
+ * alloc_fn is NULL the library uses cudaMalloc / cudaFree. */
+typedef void* (*mp_alloc_fn)(void* ctx, size_t bytes);
+typedef void (*mp_free_fn)(void* ctx, void* ptr);
+
+typedef struct {
+  int32_t precision;     /* MP_FP32 or MP_FP64 */
+  int32_t init_mode;     /* MP_INIT_* */
+  int32_t n_systems;     /* >= 1 */
+  uint32_t flags;        /* MP_FLAG_* */
+  const mp_system* systems; /* host array of n_systems, copied at create */
+  int64_t n_therm;       /* thermalisation sweeps, >= 0 */
+  int64_t n_meas;        /* measurement sweeps, >= 1 */
+  uint64_t seed;         /* Philox key */
+  void* stream;          /* cudaStream_t for all work; NULL = a non-blocking
+                            stream the handle creates and owns */
+  mp_alloc_fn alloc_fn;  /* optional */
+  mp_free_fn free_fn;    /* required when alloc_fn is set */
+  void* alloc_ctx;
+  int32_t cta_threads;   /* threads per CTA: 0 = planner default, else 128..1024 */
+  int32_t threads_per_path; /* 0 = planner default, else a multiple of 32 */
+} mp_config;
+
+typedef struct mp_state* mp_handle;
+
+/* ----------------------------------------------------------------- calls -- */
+
+/* Create a handle for one system: periodic simple-cubic lattice of L^3 spins
+ * at temperature T with n_paths independent paths of n_therm thermalisation
+ * and n_meas measurement sweeps (Sec. 2.2: "a particular lattice size at a
+ * particular temperature ... a certain number of simulation paths").  FP32
+ * form, uniform-on-sphere start, CUDA-graph replay, current device, a stream
+ * of the handle's own.  *out receives the handle (NULL on error).
+ * Errors: MP_EINVAL (out NULL, L odd or outside the supported sizes, T <= 0,
+ * n_paths < 1, n_therm < 0, n_meas < 1, path ids beyond 2^32, sweeps beyond
+ * 2^32), MP_ENOMEM, MP_ECUDA. */
+int mp_create(int L, double T, double J, double h, int64_t n_paths, int64_t n_therm,
+              int64_t n_meas, uint64_t seed, mp_handle* out);
+
+/* Create a handle for a batch of systems (uneven lattice sizes allowed) that
+ * run together in one persistent launch per run.  cfg and cfg->systems are
+ * read during the call only.  Device buffers (records, estimates, work
+ * table) are allocated here through cfg->alloc_fn and owned by the handle.
+ * Errors: as mp_create, plus MP_EINVAL for n_systems < 1 or > 65535, unknown
+ * lattice/precision/init mode, a lattice too large for the precision's
+ * shared-memory kernel, alloc_fn without free_fn. */
+int mp_create_ex(const mp_config* cfg, mp_handle* out);
+
+/* Run every path of every system from its initial state: n_therm + n_meas
+ * checkerboard sweeps with fused measurement, then the cross-path reduction.
+ * Asynchronous on the handle's stream; re-running repeats the same
+ * computation (use mp_set_seed for a new ensemble).
+ * Errors: MP_EINVAL (h NULL), MP_ECUDA (launch failure). */
+int mp_run(mp_handle h);
+
+/* Change the Philox key used by the next mp_run.  No GPU work. */
+int mp_set_seed(mp_handle h, uint64_t seed);
+
+/* Copy the estimates of system `system` (0-based, in mp_config order) into
+ * the caller's *out.  Synchronises the stream.
+ * Errors: MP_EINVAL (bad index, out NULL), MP_ESTATE (no run yet),
+ * MP_ECUDA (an asynchronous error surfaced). */
+int mp_estimates(mp_handle h, int system, mp_estimates_t* out);
+
+/* Copy the per-path records of one system, MP_NREC doubles per path, path
+ * order, into host_out (capacity `cap` doubles, must be >= n_paths*MP_NREC).
+ * Synchronises.  Errors: MP_EINVAL, MP_ESTATE, MP_ECUDA. */
+int mp_paths(mp_handle h, int system, double* host_out, int64_t cap);
+
+/* Device pointers to the handle's per-path records (all systems, system
+ * order, MP_NREC doubles per path) and estimates (MP_NEST doubles per system).
+ * Owned by the handle; valid until mp_destroy; contents valid once the
+ * stream has completed a run.  Either output may be NULL. */
+int mp_device_buffers(mp_handle h, double** d_records, double** d_estimates);
+
+/* Copy the final spins of one path (3N doubles, site-major x,y,z, site index
+ * x + L(y + Lz)) into host_out (capacity cap doubles).  Requires
+ * MP_FLAG_KEEP_SPINS.  Synchronises.  Errors: MP_EINVAL, MP_ESTATE. */
+int mp_spins(mp_handle h, int system, int64_t path, double* host_out, int64_t cap);
+
+/* Fluctuation-formula backward of the per-site observables (<e>, <|m|>) of
+ * every system: for each system s,
+ *   d_grad_beta[s] = g_e[s] d<e>/dbeta + g_m[s] d<|m|>/dbeta
+ *   d_grad_h[s]    = g_e[s] d<e>/dh    + g_m[s] d<|m|>/dh
+ * with d/dbeta = -N cov(., e), d/dh = beta N cov(., m_z) over the per-path
+ * pooled moments (the estimators of C_V and chi, Eq. (cv)).  All four arrays
+ * are device memory of n_systems doubles, owned by the caller; the kernel is
+ * queued on the handle's stream after the last run.
+ * Errors: MP_EINVAL (NULL pointer), MP_ESTATE (no run yet), MP_ECUDA. */
+int mp_backward(mp_handle h, const double* d_g_e, const double* d_g_m,
+                double* d_grad_beta, double* d_grad_h);
+
+/* Device-side durations of the last run's sweep kernel and reduction kernel,
+ * from CUDA events recorded on the handle's stream.  Synchronises.
+ * Errors: MP_ESTATE (no run yet), MP_ECUDA. */
+int mp_timing(mp_handle h, double* sweep_ms, double* reduce_ms);
+
+/* Launch shape chosen for the handle: CTA threads, CTAs in the persistent
+ * grid, dynamic shared memory bytes per CTA, work items.  Any output may be
+ * NULL. */
+int mp_plan(mp_handle h, int* cta_threads, int* grid, int* smem_bytes, int* n_items);
+
+/* Philox4x32-10 of n counters: d_ctr holds 4n uint32 words (c0 c1 c2 c3 per
+ * counter), d_out receives 4n words.  Device pointers, caller-owned; queued
+ * on `stream` (cudaStream_t, NULL = legacy default).  The same device function
+ * the sweep kernels use.  Errors: MP_EINVAL (n < 0, NULL with n > 0), MP_ECUDA. */
+int mp_philox(const uint32_t* d_ctr, int64_t n, uint64_t seed, uint32_t* d_out, void* stream);
+
+/* Release every device buffer, event and graph of the handle (after
+ * synchronising its stream).  NULL is a no-op. */
+void mp_destroy(mp_handle h);
+
+/* Text of the last error on the handle ("" if none); valid until the next
+ * call on the handle.  NULL handle: the last error of a failed create on this
+ * thread. */
+const char* mp_last_error(mp_handle h);
+
+/* Name of a status code. */
+const char* mp_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MP_H */

@@ -1,0 +1,61 @@
+// Shared device-side types of the multipath Metropolis library.
+#pragma once
+#include <cstdint>
+
+#include "mp.h"
+
+namespace mpk {
+
+constexpr uint32_t kTagUpdate = 0u;  // counter tag of the sweep updates
+constexpr uint32_t kTagInit = 1u;    // counter tag of the initial state
+
+constexpr int kSmemMax = 232448;     // 227 KB opt-in shared memory per CTA
+constexpr int kAccDoubles = 16;      // FP64 per-path accumulators in shared memory
+constexpr int kRedSlots = 4;         // doubles per warp in the per-sweep reduction
+constexpr int kMaxCta = 1024;
+
+// One system (lattice, size, temperature, couplings) of a batch, with the
+// launch shape the planner chose for it.
+struct DevSystem {
+  int32_t lattice;      // MP_LATTICE_*
+  int32_t L;
+  int32_t N;            // sites
+  int32_t NH;           // sites of the larger colour (ceil(N/2))
+  int32_t tp;           // threads per path (multiple of 32)
+  int32_t g;            // paths per CTA
+  int32_t slice_bytes;  // shared memory per path
+  int32_t pad;
+  double T, J, h, beta;
+  int64_t rec_offset;   // global index of this system's path 0
+  int64_t n_paths;
+};
+
+// A unit of the persistent work queue: `count` consecutive paths of one
+// system, run side by side by one CTA (one thread group per path).
+struct WorkItem {
+  int32_t sys;
+  int32_t count;
+  int64_t path0;
+};
+
+struct SweepParams {
+  const DevSystem* systems;
+  const WorkItem* items;
+  int* queue;             // work counter, zeroed before each launch
+  double* records;        // MP_NREC doubles per path, global path order
+  double* spins;          // optional final spins, 3N doubles per path
+  const int64_t* spin_offset;  // per-system offset (doubles) into spins
+  int32_t n_items;
+  int32_t init_mode;
+  uint32_t k0, k1;        // Philox key (seed low, seed high)
+  int64_t n_therm, n_meas;
+};
+
+// Byte offsets inside one path's shared-memory slice.
+__host__ __device__ constexpr int slice_acc_offset() { return 0; }
+__host__ __device__ constexpr int slice_red_offset() { return kAccDoubles * 8; }
+__host__ __device__ inline int slice_spin_offset(int tp) {
+  return kAccDoubles * 8 + ((tp / 32) * kRedSlots * 8 + 127) / 128 * 128;
+}
+
+}  // namespace mpk

@@ -1,0 +1,41 @@
+// Host-side launchers of the library's kernels (internal interface between the
+// C ABI in mp_api.cu and the kernel translation units).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace mpk {
+
+struct ReduceParams {
+  const DevSystem* systems;
+  const double* records;
+  double* est;  // MP_NEST doubles per system
+  int64_t n_therm, n_meas;
+};
+
+struct BackwardParams {
+  const DevSystem* systems;
+  const double* records;
+  const double* g_e;
+  const double* g_m;
+  double* grad_beta;
+  double* grad_h;
+};
+
+// shared-memory sweep kernels, one per precision
+bool sweep_supports_L(int precision, int L);
+cudaError_t sweep_prepare(int precision);  // raise the dynamic shared memory limit
+cudaError_t sweep_occupancy(int precision, int cta, int smem, int* blocks_per_sm);
+cudaError_t launch_sweep(int precision, const SweepParams& p, int grid, int cta, int smem,
+                         cudaStream_t st);
+
+cudaError_t reduce_prepare();  // raise the dynamic shared memory limit
+cudaError_t launch_reduce(const ReduceParams& p, int n_systems, int64_t max_paths, cudaStream_t st);
+cudaError_t launch_backward(const BackwardParams& p, int n_systems, cudaStream_t st);
+cudaError_t launch_philox(const uint32_t* ctr, int64_t n, uint64_t seed, uint32_t* out,
+                          cudaStream_t st);
+
+}  // namespace mpk

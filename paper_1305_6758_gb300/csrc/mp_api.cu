@@ -1,0 +1,572 @@
+// C ABI of the multipath Metropolis library (declared in include/mp.h).
+//
+// A handle owns the plan of one batch of systems: the per-system launch shape
+// (threads per path, paths per CTA, shared-memory slice), the persistent work
+// queue, the device buffers (per-path records, estimates, optional final
+// spins) and, with MP_FLAG_GRAPH, a CUDA graph of one run: zero the queue,
+// the sweep kernel, the reduction kernel, with timing events between them.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "mp.h"
+
+namespace mpk {
+
+bool sweep_supports_L_fp32(int L);
+bool sweep_supports_L_fp64(int L);
+cudaError_t sweep_prepare_fp32();
+cudaError_t sweep_prepare_fp64();
+cudaError_t sweep_occupancy_fp32(int cta, int smem, int* blocks);
+cudaError_t sweep_occupancy_fp64(int cta, int smem, int* blocks);
+cudaError_t launch_sweep_fp32(const SweepParams& p, int grid, int cta, int smem, cudaStream_t st);
+cudaError_t launch_sweep_fp64(const SweepParams& p, int grid, int cta, int smem, cudaStream_t st);
+
+bool sweep_supports_L(int precision, int L) {
+  return precision == MP_FP64 ? sweep_supports_L_fp64(L) : sweep_supports_L_fp32(L);
+}
+cudaError_t sweep_prepare(int precision) {
+  return precision == MP_FP64 ? sweep_prepare_fp64() : sweep_prepare_fp32();
+}
+cudaError_t sweep_occupancy(int precision, int cta, int smem, int* blocks) {
+  return precision == MP_FP64 ? sweep_occupancy_fp64(cta, smem, blocks)
+                              : sweep_occupancy_fp32(cta, smem, blocks);
+}
+cudaError_t launch_sweep(int precision, const SweepParams& p, int grid, int cta, int smem,
+                         cudaStream_t st) {
+  return precision == MP_FP64 ? launch_sweep_fp64(p, grid, cta, smem, st)
+                              : launch_sweep_fp32(p, grid, cta, smem, st);
+}
+
+}  // namespace mpk
+
+using namespace mpk;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int64_t sites_of(const mp_system& s) {
+  return s.lattice == MP_LATTICE_SC ? static_cast<int64_t>(s.L) * s.L * s.L : s.L;
+}
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+struct mp_state {
+  int device = 0;
+  int precision = MP_FP32;
+  int init_mode = MP_INIT_SPHERE;
+  uint32_t flags = 0;
+  int64_t n_therm = 0, n_meas = 1;
+  uint64_t seed = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  mp_alloc_fn alloc_fn = nullptr;
+  mp_free_fn free_fn = nullptr;
+  void* alloc_ctx = nullptr;
+
+  std::vector<mp_system> systems;
+  std::vector<DevSystem> hsys;
+  std::vector<WorkItem> items;
+  std::vector<int64_t> spin_offset;
+  int64_t total_paths = 0, max_paths = 0, total_spins = 0;
+
+  int cta = 0, grid = 0, smem = 0;
+
+  DevSystem* d_sys = nullptr;
+  WorkItem* d_items = nullptr;
+  int* d_queue = nullptr;
+  double* d_rec = nullptr;
+  double* d_est = nullptr;
+  double* d_spins = nullptr;
+  int64_t* d_spin_offset = nullptr;
+  std::vector<void*> owned;
+
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_dirty = true;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  bool ran = false;
+  std::string err;
+};
+
+namespace {
+
+int fail(mp_state* h, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf;
+  else g_create_error = buf;
+  return code;
+}
+
+int cuda_fail(mp_state* h, cudaError_t e, const char* what) {
+  return fail(h, MP_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define MP_CUDA(h, call)                                  \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+  } while (0)
+
+// Makes the handle's device current for the scope and restores the caller's.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+void* dev_alloc(mp_state* h, size_t bytes) {
+  bytes = (bytes + 255) / 256 * 256;
+  void* p = nullptr;
+  if (h->alloc_fn) {
+    p = h->alloc_fn(h->alloc_ctx, bytes);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) h->owned.push_back(p);
+  return p;
+}
+
+void release(mp_state* h) {
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  for (auto& e : h->ev)
+    if (e) cudaEventDestroy(e);
+  for (void* p : h->owned) {
+    if (h->alloc_fn) h->free_fn(h->alloc_ctx, p);
+    else cudaFree(p);
+  }
+  h->owned.clear();
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+int validate(const mp_config* cfg) {
+  if (!cfg) return fail(nullptr, MP_EINVAL, "config is NULL");
+  if (cfg->precision != MP_FP32 && cfg->precision != MP_FP64)
+    return fail(nullptr, MP_EINVAL, "unknown precision %d", cfg->precision);
+  if (cfg->init_mode < MP_INIT_SPHERE || cfg->init_mode > MP_INIT_ORDERED)
+    return fail(nullptr, MP_EINVAL, "unknown init mode %d", cfg->init_mode);
+  if (cfg->n_systems < 1 || cfg->n_systems > 65535 || !cfg->systems)
+    return fail(nullptr, MP_EINVAL, "n_systems must be in 1..65535 with a systems array");
+  if (cfg->n_therm < 0 || cfg->n_meas < 1)
+    return fail(nullptr, MP_EINVAL, "need n_therm >= 0 and n_meas >= 1");
+  if (cfg->n_therm + cfg->n_meas > 0xffffffffLL)
+    return fail(nullptr, MP_EINVAL, "more than 2^32-1 sweeps");
+  if (cfg->alloc_fn && !cfg->free_fn) return fail(nullptr, MP_EINVAL, "alloc_fn without free_fn");
+  if (cfg->cta_threads != 0 &&
+      (cfg->cta_threads < 32 || cfg->cta_threads > kMaxCta || cfg->cta_threads % 32))
+    return fail(nullptr, MP_EINVAL, "cta_threads must be a multiple of 32 in 32..1024");
+  if (cfg->threads_per_path != 0 &&
+      (cfg->threads_per_path < 32 || cfg->threads_per_path > kMaxCta || cfg->threads_per_path % 32))
+    return fail(nullptr, MP_EINVAL, "threads_per_path must be a multiple of 32 in 32..1024");
+  for (int k = 0; k < cfg->n_systems; ++k) {
+    const mp_system& s = cfg->systems[k];
+    if (s.lattice != MP_LATTICE_SC && s.lattice != MP_LATTICE_CHAIN)
+      return fail(nullptr, MP_EINVAL, "system %d: unknown lattice %d", k, s.lattice);
+    if (!(s.T > 0.0) || !std::isfinite(s.T) || !std::isfinite(s.J) || !std::isfinite(s.h))
+      return fail(nullptr, MP_EINVAL, "system %d: need finite T > 0, J, h", k);
+    if (s.n_paths < 1 || s.n_paths > 0x7fffffffLL)
+      return fail(nullptr, MP_EINVAL, "system %d: n_paths must be in 1..2^31-1", k);
+    if (s.lattice == MP_LATTICE_SC) {
+      if (s.L < 2 || (s.L & 1))
+        return fail(nullptr, MP_EINVAL, "system %d: simple cubic L must be even and >= 2", k);
+      if (!sweep_supports_L(cfg->precision, s.L))
+        return fail(nullptr, MP_EINVAL,
+                    "system %d: L=%d does not fit the %s shared-memory sweep", k, s.L,
+                    cfg->precision == MP_FP64 ? "FP64" : "FP32");
+    } else if (s.L < 2 || s.L > 8192) {
+      return fail(nullptr, MP_EINVAL, "system %d: chain length must be in 2..8192", k);
+    }
+  }
+  return MP_OK;
+}
+
+// Launch shape: threads per path from the sites per colour (about 8 sites per
+// thread per half-sweep), paths per CTA from the CTA size, the named-barrier
+// budget and shared memory; the CTA shrinks while there are too few work
+// items to cover every SM twice.
+int plan(mp_state* h, const mp_config* cfg) {
+  const int real = h->precision == MP_FP64 ? 8 : 4;
+  const int cta_max = h->precision == MP_FP64 ? 512 : kMaxCta;  // CtaLimit of the sweep kernel
+  int sms = 0;
+  MP_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+  const int n = static_cast<int>(h->systems.size());
+  std::vector<int> tp(n), slice(n);
+  int max_tp = 32;
+  for (int k = 0; k < n; ++k) {
+    const int64_t N = sites_of(h->systems[k]);
+    const int NH = static_cast<int>((N + 1) / 2);
+    int t = cfg->threads_per_path;
+    if (t == 0) t = std::min(cta_max, std::max(32, round_up((NH + 7) / 8, 32)));
+    if (t > cta_max) return fail(h, MP_EINVAL, "threads_per_path %d above %d", t, cta_max);
+    tp[k] = t;
+    slice[k] = round_up(slice_spin_offset(t) + 6 * NH * real, 128);
+    if (slice[k] > kSmemMax)
+      return fail(h, MP_EINVAL, "system %d needs %d bytes of shared memory per path (max %d)", k,
+                  slice[k], kSmemMax);
+    max_tp = std::max(max_tp, t);
+  }
+  auto paths_per_cta = [&](int k, int cta) {
+    int g = cta / tp[k];
+    if (tp[k] > 32) g = std::min(g, 15);  // named barriers 1..15
+    g = std::min<int64_t>(g, kSmemMax / slice[k]);
+    g = static_cast<int>(std::min<int64_t>(g, h->systems[k].n_paths));
+    return std::max(g, 1);
+  };
+  auto count_items = [&](int cta) {
+    int64_t items = 0;
+    for (int k = 0; k < n; ++k) {
+      const int g = paths_per_cta(k, cta);
+      items += (h->systems[k].n_paths + g - 1) / g;
+    }
+    return items;
+  };
+  int cta = cfg->cta_threads;
+  if (cta > cta_max) return fail(h, MP_EINVAL, "cta_threads %d above %d for this precision", cta, cta_max);
+  if (cta == 0) {
+    cta = cta_max;
+    while (cta / 2 >= std::max(max_tp, 128) && count_items(cta) < 2LL * sms) cta /= 2;
+  }
+  if (cta < max_tp) return fail(h, MP_EINVAL, "cta_threads %d below threads per path %d", cta, max_tp);
+
+  h->hsys.resize(n);
+  h->items.clear();
+  h->spin_offset.assign(n, 0);
+  int smem = 0;
+  int64_t rec = 0, spins = 0;
+  for (int k = 0; k < n; ++k) {
+    const mp_system& s = h->systems[k];
+    DevSystem& d = h->hsys[k];
+    d.lattice = s.lattice;
+    d.L = s.L;
+    d.N = static_cast<int32_t>(sites_of(s));
+    d.NH = (d.N + 1) / 2;
+    d.tp = tp[k];
+    d.g = paths_per_cta(k, cta);
+    d.slice_bytes = slice[k];
+    d.pad = 0;
+    d.T = s.T;
+    d.J = s.J;
+    d.h = s.h;
+    d.beta = 1.0 / s.T;
+    d.rec_offset = rec;
+    d.n_paths = s.n_paths;
+    rec += s.n_paths;
+    h->spin_offset[k] = spins;
+    spins += s.n_paths * 3 * static_cast<int64_t>(d.N);
+    smem = std::max(smem, d.g * d.slice_bytes);
+    for (int64_t p0 = 0; p0 < s.n_paths; p0 += d.g)
+      h->items.push_back(WorkItem{k, static_cast<int32_t>(std::min<int64_t>(d.g, s.n_paths - p0)), p0});
+    h->max_paths = std::max(h->max_paths, s.n_paths);
+  }
+  // largest lattices first, so the persistent CTAs finish together
+  std::stable_sort(h->items.begin(), h->items.end(), [&](const WorkItem& a, const WorkItem& b) {
+    return h->hsys[a.sys].N > h->hsys[b.sys].N;
+  });
+  if (h->items.size() > 0x7fffffffULL) return fail(h, MP_EINVAL, "too many work items");
+  h->total_paths = rec;
+  h->total_spins = spins;
+  h->cta = cta;
+  h->smem = smem;
+  MP_CUDA(h, sweep_prepare(h->precision));
+  MP_CUDA(h, reduce_prepare());
+  int per_sm = 0;
+  MP_CUDA(h, sweep_occupancy(h->precision, cta, smem, &per_sm));
+  if (per_sm < 1) return fail(h, MP_EINVAL, "launch shape %d threads x %d bytes does not fit an SM", cta, smem);
+  h->grid = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(h->items.size()),
+                                               static_cast<int64_t>(sms) * per_sm));
+  return MP_OK;
+}
+
+int enqueue_run(mp_state* h) {
+  SweepParams p{};
+  p.systems = h->d_sys;
+  p.items = h->d_items;
+  p.queue = h->d_queue;
+  p.records = h->d_rec;
+  p.spins = h->d_spins;
+  p.spin_offset = h->d_spin_offset;
+  p.n_items = static_cast<int32_t>(h->items.size());
+  p.init_mode = h->init_mode;
+  p.k0 = static_cast<uint32_t>(h->seed & 0xffffffffu);
+  p.k1 = static_cast<uint32_t>(h->seed >> 32);
+  p.n_therm = h->n_therm;
+  p.n_meas = h->n_meas;
+  ReduceParams r{};
+  r.systems = h->d_sys;
+  r.records = h->d_rec;
+  r.est = h->d_est;
+  r.n_therm = h->n_therm;
+  r.n_meas = h->n_meas;
+  const bool capturing = h->flags & MP_FLAG_GRAPH;
+  const unsigned evflag = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+  MP_CUDA(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int), h->stream));
+  MP_CUDA(h, cudaEventRecordWithFlags(h->ev[0], h->stream, evflag));
+  MP_CUDA(h, launch_sweep(h->precision, p, h->grid, h->cta, h->smem, h->stream));
+  MP_CUDA(h, cudaEventRecordWithFlags(h->ev[1], h->stream, evflag));
+  MP_CUDA(h, launch_reduce(r, static_cast<int>(h->hsys.size()), h->max_paths, h->stream));
+  MP_CUDA(h, cudaEventRecordWithFlags(h->ev[2], h->stream, evflag));
+  return MP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mp_create(int L, double T, double J, double h, int64_t n_paths, int64_t n_therm, int64_t n_meas,
+              uint64_t seed, mp_handle* out) {
+  mp_system s{MP_LATTICE_SC, L, T, J, h, n_paths};
+  mp_config cfg{};
+  cfg.precision = MP_FP32;
+  cfg.init_mode = MP_INIT_SPHERE;
+  cfg.n_systems = 1;
+  cfg.flags = MP_FLAG_GRAPH;
+  cfg.systems = &s;
+  cfg.n_therm = n_therm;
+  cfg.n_meas = n_meas;
+  cfg.seed = seed;
+  return mp_create_ex(&cfg, out);
+}
+
+int mp_create_ex(const mp_config* cfg, mp_handle* out) {
+  g_create_error.clear();
+  if (!out) return fail(nullptr, MP_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate(cfg);
+  if (rc != MP_OK) return rc;
+  mp_state* h = new mp_state();
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return fail(nullptr, MP_ECUDA, "no CUDA device");
+  }
+  h->precision = cfg->precision;
+  h->init_mode = cfg->init_mode;
+  h->flags = cfg->flags;
+  h->n_therm = cfg->n_therm;
+  h->n_meas = cfg->n_meas;
+  h->seed = cfg->seed;
+  h->alloc_fn = cfg->alloc_fn;
+  h->free_fn = cfg->free_fn;
+  h->alloc_ctx = cfg->alloc_ctx;
+  h->systems.assign(cfg->systems, cfg->systems + cfg->n_systems);
+  auto bail = [&](int code) {
+    g_create_error = h->err;
+    release(h);
+    delete h;
+    return code;
+  };
+  if (cfg->stream) {
+    h->stream = static_cast<cudaStream_t>(cfg->stream);
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaStreamCreateWithFlags"));
+    h->own_stream = true;
+  }
+  rc = plan(h, cfg);
+  if (rc != MP_OK) return bail(rc);
+  for (auto& e : h->ev) {
+    cudaError_t ce = cudaEventCreate(&e);
+    if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "cudaEventCreate"));
+  }
+  const int n = static_cast<int>(h->hsys.size());
+  h->d_sys = static_cast<DevSystem*>(dev_alloc(h, sizeof(DevSystem) * n));
+  h->d_items = static_cast<WorkItem*>(dev_alloc(h, sizeof(WorkItem) * h->items.size()));
+  h->d_queue = static_cast<int*>(dev_alloc(h, 256));
+  h->d_rec = static_cast<double*>(dev_alloc(h, sizeof(double) * MP_NREC * h->total_paths));
+  h->d_est = static_cast<double*>(dev_alloc(h, sizeof(double) * MP_NEST * n));
+  h->d_spin_offset = static_cast<int64_t*>(dev_alloc(h, sizeof(int64_t) * n));
+  if (!h->d_sys || !h->d_items || !h->d_queue || !h->d_rec || !h->d_est || !h->d_spin_offset)
+    return bail(fail(h, MP_ENOMEM, "device allocation failed"));
+  if (h->flags & MP_FLAG_KEEP_SPINS) {
+    h->d_spins = static_cast<double*>(dev_alloc(h, sizeof(double) * h->total_spins));
+    if (!h->d_spins) return bail(fail(h, MP_ENOMEM, "spin buffer allocation failed"));
+  }
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(h->d_sys, h->hsys.data(), sizeof(DevSystem) * n, cudaMemcpyHostToDevice,
+                           h->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h->d_items, h->items.data(), sizeof(WorkItem) * h->items.size(),
+                           cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h->d_spin_offset, h->spin_offset.data(), sizeof(int64_t) * n,
+                           cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+    return bail(cuda_fail(h, e, "uploading the work tables"));
+  *out = h;
+  return MP_OK;
+}
+
+int mp_run(mp_handle h) {
+  if (!h) return fail(nullptr, MP_EINVAL, "handle is NULL");
+  DeviceGuard dg(h->device);
+  if (!(h->flags & MP_FLAG_GRAPH)) {
+    int rc = enqueue_run(h);
+    if (rc != MP_OK) return rc;
+    h->ran = true;
+    return MP_OK;
+  }
+  if (h->graph_dirty || !h->gexec) {
+    if (h->gexec) {
+      cudaGraphExecDestroy(h->gexec);
+      h->gexec = nullptr;
+    }
+    MP_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_run(h);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    if (rc != MP_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+    h->graph_dirty = false;
+  }
+  MP_CUDA(h, cudaGraphLaunch(h->gexec, h->stream));
+  h->ran = true;
+  return MP_OK;
+}
+
+int mp_set_seed(mp_handle h, uint64_t seed) {
+  if (!h) return fail(nullptr, MP_EINVAL, "handle is NULL");
+  if (seed != h->seed) {
+    h->seed = seed;
+    h->graph_dirty = true;
+  }
+  return MP_OK;
+}
+
+int mp_estimates(mp_handle h, int system, mp_estimates_t* out) {
+  if (!h) return fail(nullptr, MP_EINVAL, "handle is NULL");
+  if (!out || system < 0 || system >= static_cast<int>(h->hsys.size()))
+    return fail(h, MP_EINVAL, "bad system index %d or NULL output", system);
+  if (!h->ran) return fail(h, MP_ESTATE, "no run yet");
+  DeviceGuard dg(h->device);
+  MP_CUDA(h, cudaMemcpyAsync(out, h->d_est + static_cast<int64_t>(system) * MP_NEST,
+                             sizeof(mp_estimates_t), cudaMemcpyDeviceToHost, h->stream));
+  MP_CUDA(h, cudaStreamSynchronize(h->stream));
+  return MP_OK;
+}
+
+int mp_paths(mp_handle h, int system, double* host_out, int64_t cap) {
+  if (!h) return fail(nullptr, MP_EINVAL, "handle is NULL");
+  if (!host_out || system < 0 || system >= static_cast<int>(h->hsys.size()))
+    return fail(h, MP_EINVAL, "bad system index %d or NULL output", system);
+  const DevSystem& d = h->hsys[system];
+  if (cap < d.n_paths * MP_NREC) return fail(h, MP_EINVAL, "capacity %lld below %lld", (long long)cap,
+                                            (long long)(d.n_paths * MP_NREC));
+  if (!h->ran) return fail(h, MP_ESTATE, "no run yet");
+  DeviceGuard dg(h->device);
+  MP_CUDA(h, cudaMemcpyAsync(host_out, h->d_rec + d.rec_offset * MP_NREC,
+                             sizeof(double) * MP_NREC * d.n_paths, cudaMemcpyDeviceToHost, h->stream));
+  MP_CUDA(h, cudaStreamSynchronize(h->stream));
+  return MP_OK;
+}
+
+int mp_device_buffers(mp_handle h, double** d_records, double** d_estimates) {
+  if (!h) return fail(nullptr, MP_EINVAL, "handle is NULL");
+  if (d_records) *d_records = h->d_rec;
+  if (d_estimates) *d_estimates = h->d_est;
+  return MP_OK;
+}
+
+int mp_spins(mp_handle h, int system, int64_t path, double* host_out, int64_t cap) {
+  if (!h) return fail(nullptr, MP_EINVAL, "handle is NULL");
+  if (!(h->flags & MP_FLAG_KEEP_SPINS)) return fail(h, MP_ESTATE, "created without MP_FLAG_KEEP_SPINS");
+  if (!host_out || system < 0 || system >= static_cast<int>(h->hsys.size()))
+    return fail(h, MP_EINVAL, "bad system index %d or NULL output", system);
+  const DevSystem& d = h->hsys[system];
+  if (path < 0 || path >= d.n_paths) return fail(h, MP_EINVAL, "path %lld out of range", (long long)path);
+  const int64_t n = 3 * static_cast<int64_t>(d.N);
+  if (cap < n) return fail(h, MP_EINVAL, "capacity %lld below %lld", (long long)cap, (long long)n);
+  if (!h->ran) return fail(h, MP_ESTATE, "no run yet");
+  DeviceGuard dg(h->device);
+  MP_CUDA(h, cudaMemcpyAsync(host_out, h->d_spins + h->spin_offset[system] + path * n,
+                             sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+  MP_CUDA(h, cudaStreamSynchronize(h->stream));
+  return MP_OK;
+}
+
+int mp_backward(mp_handle h, const double* d_g_e, const double* d_g_m, double* d_grad_beta,
+                double* d_grad_h) {
+  if (!h) return fail(nullptr, MP_EINVAL, "handle is NULL");
+  if (!d_g_e || !d_g_m || !d_grad_beta || !d_grad_h) return fail(h, MP_EINVAL, "NULL gradient buffer");
+  if (!h->ran) return fail(h, MP_ESTATE, "no run yet");
+  DeviceGuard dg(h->device);
+  BackwardParams p{h->d_sys, h->d_rec, d_g_e, d_g_m, d_grad_beta, d_grad_h};
+  MP_CUDA(h, launch_backward(p, static_cast<int>(h->hsys.size()), h->stream));
+  return MP_OK;
+}
+
+int mp_timing(mp_handle h, double* sweep_ms, double* reduce_ms) {
+  if (!h) return fail(nullptr, MP_EINVAL, "handle is NULL");
+  if (!h->ran) return fail(h, MP_ESTATE, "no run yet");
+  DeviceGuard dg(h->device);
+  MP_CUDA(h, cudaStreamSynchronize(h->stream));
+  float a = 0.f, b = 0.f;
+  MP_CUDA(h, cudaEventElapsedTime(&a, h->ev[0], h->ev[1]));
+  MP_CUDA(h, cudaEventElapsedTime(&b, h->ev[1], h->ev[2]));
+  if (sweep_ms) *sweep_ms = a;
+  if (reduce_ms) *reduce_ms = b;
+  return MP_OK;
+}
+
+int mp_plan(mp_handle h, int* cta_threads, int* grid, int* smem_bytes, int* n_items) {
+  if (!h) return fail(nullptr, MP_EINVAL, "handle is NULL");
+  if (cta_threads) *cta_threads = h->cta;
+  if (grid) *grid = h->grid;
+  if (smem_bytes) *smem_bytes = h->smem;
+  if (n_items) *n_items = static_cast<int>(h->items.size());
+  return MP_OK;
+}
+
+int mp_philox(const uint32_t* d_ctr, int64_t n, uint64_t seed, uint32_t* d_out, void* stream) {
+  if (n < 0 || (n > 0 && (!d_ctr || !d_out))) return fail(nullptr, MP_EINVAL, "bad Philox arguments");
+  cudaError_t e = launch_philox(d_ctr, n, seed, d_out, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "philox kernel");
+  return MP_OK;
+}
+
+void mp_destroy(mp_handle h) {
+  if (!h) return;
+  DeviceGuard dg(h->device);
+  release(h);
+  delete h;
+}
+
+const char* mp_last_error(mp_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+const char* mp_status_string(int status) {
+  switch (status) {
+    case MP_OK: return "MP_OK";
+    case MP_EINVAL: return "MP_EINVAL";
+    case MP_ENOMEM: return "MP_ENOMEM";
+    case MP_ECUDA: return "MP_ECUDA";
+    case MP_ESTATE: return "MP_ESTATE";
+    case MP_ECANCELED: return "MP_ECANCELED";
+    case MP_ETIMEOUT: return "MP_ETIMEOUT";
+    default: return "MP_E?";
+  }
+}
+
+}  // extern "C"
