@@ -191,8 +191,8 @@ class Simulation:
     """A handle of the library: a batch of systems run together.
 
     Device memory comes from PyTorch's allocator on ``device`` (default
-    ``cuda:0``); work runs on the PyTorch current stream of that device unless
-    ``stream`` (a ``torch.cuda.Stream``) is given.
+    ``cuda:0``); all work runs on ``self.stream``, a new ``torch.cuda.Stream``
+    unless ``stream`` is given.
     """
 
     def __init__(self, systems: list[System], n_therm: int, n_meas: int, seed: int = 1,
@@ -208,7 +208,8 @@ class Simulation:
         self._sys = (MPSystem * len(systems))(
             *[MPSystem(s.lattice, s.L, s.T, s.J, s.h, s.n_paths) for s in systems])
         self._alloc = _TorchAllocator(self.device)
-        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        # a stream of its own (PyTorch's default stream is the legacy NULL stream)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
         cfg = MPConfig()
         cfg.precision = precision
         cfg.init_mode = init_mode
@@ -292,12 +293,18 @@ class Simulation:
         """Fluctuation-formula gradients (d/dbeta, d/dh) of g_e.<e> + g_m.<|m|> per system."""
         torch = self.torch
         n = len(self.systems)
-        ge = torch.as_tensor(g_e, dtype=torch.float64, device=self.device).reshape(n).contiguous()
-        gm = torch.as_tensor(g_m, dtype=torch.float64, device=self.device).reshape(n).contiguous()
-        gb = torch.empty(n, dtype=torch.float64, device=self.device)
-        gh = torch.empty(n, dtype=torch.float64, device=self.device)
-        _check(_lib.mp_backward(self._h, ge.data_ptr(), gm.data_ptr(), gb.data_ptr(), gh.data_ptr()),
-               self._h)
+        caller = torch.cuda.current_stream(self.device)
+        self.stream.wait_stream(caller)  # gradients the caller produced are ready
+        with torch.cuda.stream(self.stream):
+            ge = torch.as_tensor(g_e, dtype=torch.float64, device=self.device).reshape(n).contiguous()
+            gm = torch.as_tensor(g_m, dtype=torch.float64, device=self.device).reshape(n).contiguous()
+            gb = torch.empty(n, dtype=torch.float64, device=self.device)
+            gh = torch.empty(n, dtype=torch.float64, device=self.device)
+            _check(_lib.mp_backward(self._h, ge.data_ptr(), gm.data_ptr(), gb.data_ptr(), gh.data_ptr()),
+                   self._h)
+        caller.wait_stream(self.stream)  # results are ready on the caller's stream
+        for t in (ge, gm, gb, gh):
+            t.record_stream(self.stream)
         return gb, gh
 
     def timing(self) -> tuple[float, float]:

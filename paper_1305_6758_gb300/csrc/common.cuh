@@ -3,14 +3,14 @@
 #include <cstdint>
 
 #include "mp.h"
+#include "philox.cuh"
 
 namespace mpk {
 
 constexpr uint32_t kTagUpdate = 0u;  // counter tag of the sweep updates
 constexpr uint32_t kTagInit = 1u;    // counter tag of the initial state
 
-constexpr int kSmemMax = 232448;     // 227 KB opt-in shared memory per CTA
-constexpr int kAccDoubles = 16;      // FP64 per-path accumulators in shared memory
+constexpr int kAccDoubles = 24;      // FP64 per-path accumulators (>= MP_NREC) in shared memory
 constexpr int kRedSlots = 4;         // doubles per warp in the per-sweep reduction
 constexpr int kMaxCta = 1024;
 
@@ -47,8 +47,8 @@ struct SweepParams {
   const int64_t* spin_offset;  // per-system offset (doubles) into spins
   int32_t n_items;
   int32_t init_mode;
-  uint32_t k0, k1;        // Philox key (seed low, seed high)
   int64_t n_therm, n_meas;
+  PhiloxKeys key;         // round keys of the seed
 };
 
 // Byte offsets inside one path's shared-memory slice.
@@ -58,4 +58,9 @@ __host__ __device__ inline int slice_spin_offset(int tp) {
   return kAccDoubles * 8 + ((tp / 32) * kRedSlots * 8 + 127) / 128 * 128;
 }
 
+}  // namespace mpk
+
+namespace mpk {
+static_assert(kAccDoubles >= MP_NREC, "accumulators must hold a whole record");
+static_assert(kAccDoubles <= 32, "accumulators are zeroed by the first warp");
 }  // namespace mpk

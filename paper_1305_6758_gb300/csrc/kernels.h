@@ -25,12 +25,14 @@ struct BackwardParams {
   double* grad_h;
 };
 
-// shared-memory sweep kernels, one per precision
+// Shared-memory sweep kernels.  `variant` selects the kernel: L > 0 a batch
+// of simple cubic lattices of that one size, -1 open chains only, 0 a batch
+// of uneven sizes (the kernel switches per work item).
 bool sweep_supports_L(int precision, int L);
-cudaError_t sweep_prepare(int precision);  // raise the dynamic shared memory limit
-cudaError_t sweep_occupancy(int precision, int cta, int smem, int* blocks_per_sm);
-cudaError_t launch_sweep(int precision, const SweepParams& p, int grid, int cta, int smem,
-                         cudaStream_t st);
+cudaError_t sweep_prepare(int precision, int variant, int device, int* max_dynamic);
+cudaError_t sweep_occupancy(int precision, int variant, int cta, int smem, int* blocks_per_sm);
+cudaError_t launch_sweep(int precision, int variant, const SweepParams& p, int grid, int cta,
+                         int smem, cudaStream_t st);
 
 cudaError_t reduce_prepare();  // raise the dynamic shared memory limit
 cudaError_t launch_reduce(const ReduceParams& p, int n_systems, int64_t max_paths, cudaStream_t st);

@@ -22,27 +22,30 @@ namespace mpk {
 
 bool sweep_supports_L_fp32(int L);
 bool sweep_supports_L_fp64(int L);
-cudaError_t sweep_prepare_fp32();
-cudaError_t sweep_prepare_fp64();
-cudaError_t sweep_occupancy_fp32(int cta, int smem, int* blocks);
-cudaError_t sweep_occupancy_fp64(int cta, int smem, int* blocks);
-cudaError_t launch_sweep_fp32(const SweepParams& p, int grid, int cta, int smem, cudaStream_t st);
-cudaError_t launch_sweep_fp64(const SweepParams& p, int grid, int cta, int smem, cudaStream_t st);
+cudaError_t sweep_prepare_fp32(int variant, int device, int* max_dynamic);
+cudaError_t sweep_prepare_fp64(int variant, int device, int* max_dynamic);
+cudaError_t sweep_occupancy_fp32(int variant, int cta, int smem, int* blocks);
+cudaError_t sweep_occupancy_fp64(int variant, int cta, int smem, int* blocks);
+cudaError_t launch_sweep_fp32(int variant, const SweepParams& p, int grid, int cta, int smem,
+                              cudaStream_t st);
+cudaError_t launch_sweep_fp64(int variant, const SweepParams& p, int grid, int cta, int smem,
+                              cudaStream_t st);
 
 bool sweep_supports_L(int precision, int L) {
   return precision == MP_FP64 ? sweep_supports_L_fp64(L) : sweep_supports_L_fp32(L);
 }
-cudaError_t sweep_prepare(int precision) {
-  return precision == MP_FP64 ? sweep_prepare_fp64() : sweep_prepare_fp32();
+cudaError_t sweep_prepare(int precision, int variant, int device, int* max_dynamic) {
+  return precision == MP_FP64 ? sweep_prepare_fp64(variant, device, max_dynamic)
+                              : sweep_prepare_fp32(variant, device, max_dynamic);
 }
-cudaError_t sweep_occupancy(int precision, int cta, int smem, int* blocks) {
-  return precision == MP_FP64 ? sweep_occupancy_fp64(cta, smem, blocks)
-                              : sweep_occupancy_fp32(cta, smem, blocks);
+cudaError_t sweep_occupancy(int precision, int variant, int cta, int smem, int* blocks) {
+  return precision == MP_FP64 ? sweep_occupancy_fp64(variant, cta, smem, blocks)
+                              : sweep_occupancy_fp32(variant, cta, smem, blocks);
 }
-cudaError_t launch_sweep(int precision, const SweepParams& p, int grid, int cta, int smem,
-                         cudaStream_t st) {
-  return precision == MP_FP64 ? launch_sweep_fp64(p, grid, cta, smem, st)
-                              : launch_sweep_fp32(p, grid, cta, smem, st);
+cudaError_t launch_sweep(int precision, int variant, const SweepParams& p, int grid, int cta,
+                         int smem, cudaStream_t st) {
+  return precision == MP_FP64 ? launch_sweep_fp64(variant, p, grid, cta, smem, st)
+                              : launch_sweep_fp32(variant, p, grid, cta, smem, st);
 }
 
 }  // namespace mpk
@@ -81,6 +84,7 @@ struct mp_state {
   int64_t total_paths = 0, max_paths = 0, total_spins = 0;
 
   int cta = 0, grid = 0, smem = 0;
+  int variant = 0;  // sweep kernel variant (see kernels.h)
 
   DevSystem* d_sys = nullptr;
   WorkItem* d_items = nullptr;
@@ -207,28 +211,51 @@ int validate(const mp_config* cfg) {
 int plan(mp_state* h, const mp_config* cfg) {
   const int real = h->precision == MP_FP64 ? 8 : 4;
   const int cta_max = h->precision == MP_FP64 ? 512 : kMaxCta;  // CtaLimit of the sweep kernel
-  int sms = 0;
-  MP_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
   const int n = static_cast<int>(h->systems.size());
+  // one kernel per lattice size when the batch has a single size
+  int variant = h->systems[0].lattice == MP_LATTICE_CHAIN ? -1 : h->systems[0].L;
+  for (int k = 1; k < n; ++k) {
+    const int v = h->systems[k].lattice == MP_LATTICE_CHAIN ? -1 : h->systems[k].L;
+    if (v != variant) variant = 0;
+  }
+  h->variant = variant;
+  int sms = 0, smem_max = 0;
+  MP_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+  MP_CUDA(h, sweep_prepare(h->precision, variant, h->device, &smem_max));
+  MP_CUDA(h, reduce_prepare());
   std::vector<int> tp(n), slice(n);
   int max_tp = 32;
   for (int k = 0; k < n; ++k) {
     const int64_t N = sites_of(h->systems[k]);
     const int NH = static_cast<int>((N + 1) / 2);
     int t = cfg->threads_per_path;
+    if (t == 0 && h->systems[k].lattice == MP_LATTICE_SC) {
+      // a multiple of the half-sites of a z-plane lets each thread walk one
+      // column (fixed x/2, y); pick the one closest to 8 sites per thread
+      const int L = h->systems[k].L, HP = L * L / 2;
+      double best = 1e30;
+      for (int c = HP; c <= std::min(cta_max, round_up(NH, 32)); c += HP) {
+        if (c % 32) continue;
+        const double d = std::fabs(static_cast<double>(NH) / c - 8.0);
+        if (d < best) {
+          best = d;
+          t = c;
+        }
+      }
+    }
     if (t == 0) t = std::min(cta_max, std::max(32, round_up((NH + 7) / 8, 32)));
     if (t > cta_max) return fail(h, MP_EINVAL, "threads_per_path %d above %d", t, cta_max);
     tp[k] = t;
     slice[k] = round_up(slice_spin_offset(t) + 6 * NH * real, 128);
-    if (slice[k] > kSmemMax)
+    if (slice[k] > smem_max)
       return fail(h, MP_EINVAL, "system %d needs %d bytes of shared memory per path (max %d)", k,
-                  slice[k], kSmemMax);
+                  slice[k], smem_max);
     max_tp = std::max(max_tp, t);
   }
   auto paths_per_cta = [&](int k, int cta) {
     int g = cta / tp[k];
     if (tp[k] > 32) g = std::min(g, 15);  // named barriers 1..15
-    g = std::min<int64_t>(g, kSmemMax / slice[k]);
+    g = std::min<int64_t>(g, smem_max / slice[k]);
     g = static_cast<int>(std::min<int64_t>(g, h->systems[k].n_paths));
     return std::max(g, 1);
   };
@@ -287,10 +314,8 @@ int plan(mp_state* h, const mp_config* cfg) {
   h->total_spins = spins;
   h->cta = cta;
   h->smem = smem;
-  MP_CUDA(h, sweep_prepare(h->precision));
-  MP_CUDA(h, reduce_prepare());
   int per_sm = 0;
-  MP_CUDA(h, sweep_occupancy(h->precision, cta, smem, &per_sm));
+  MP_CUDA(h, sweep_occupancy(h->precision, variant, cta, smem, &per_sm));
   if (per_sm < 1) return fail(h, MP_EINVAL, "launch shape %d threads x %d bytes does not fit an SM", cta, smem);
   h->grid = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(h->items.size()),
                                                static_cast<int64_t>(sms) * per_sm));
@@ -307,8 +332,7 @@ int enqueue_run(mp_state* h) {
   p.spin_offset = h->d_spin_offset;
   p.n_items = static_cast<int32_t>(h->items.size());
   p.init_mode = h->init_mode;
-  p.k0 = static_cast<uint32_t>(h->seed & 0xffffffffu);
-  p.k1 = static_cast<uint32_t>(h->seed >> 32);
+  p.key = philox_round_keys(h->seed);
   p.n_therm = h->n_therm;
   p.n_meas = h->n_meas;
   ReduceParams r{};
@@ -321,7 +345,7 @@ int enqueue_run(mp_state* h) {
   const unsigned evflag = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   MP_CUDA(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int), h->stream));
   MP_CUDA(h, cudaEventRecordWithFlags(h->ev[0], h->stream, evflag));
-  MP_CUDA(h, launch_sweep(h->precision, p, h->grid, h->cta, h->smem, h->stream));
+  MP_CUDA(h, launch_sweep(h->precision, h->variant, p, h->grid, h->cta, h->smem, h->stream));
   MP_CUDA(h, cudaEventRecordWithFlags(h->ev[1], h->stream, evflag));
   MP_CUDA(h, launch_reduce(r, static_cast<int>(h->hsys.size()), h->max_paths, h->stream));
   MP_CUDA(h, cudaEventRecordWithFlags(h->ev[2], h->stream, evflag));

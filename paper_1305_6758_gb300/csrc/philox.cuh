@@ -17,22 +17,41 @@ struct Philox4 {
   uint32_t x, y, z, w;
 };
 
+constexpr uint32_t kPhiloxMulA = 0xD2511F53u, kPhiloxMulB = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxWeylA = 0x9E3779B9u, kPhiloxWeylB = 0xBB67AE85u;
+
+// The ten round keys of a 64-bit key: (k0 + r*WeylA, k1 + r*WeylB), r = 0..9.
+// Computed once on the host and passed as kernel parameters, so that each
+// round's key is a constant-memory operand instead of two per-thread adds.
+struct PhiloxKeys {
+  uint32_t k0[10];
+  uint32_t k1[10];
+};
+
+inline PhiloxKeys philox_round_keys(uint64_t seed) {
+  PhiloxKeys k{};
+  uint32_t a = static_cast<uint32_t>(seed & 0xffffffffu), b = static_cast<uint32_t>(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    k.k0[r] = a;
+    k.k1[r] = b;
+    a += kPhiloxWeylA;
+    b += kPhiloxWeylB;
+  }
+  return k;
+}
+
 __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
-                                                 uint32_t c3, uint32_t k0, uint32_t k1) {
-  constexpr uint32_t kMulA = 0xD2511F53u, kMulB = 0xCD9E8D57u;
-  constexpr uint32_t kWeylA = 0x9E3779B9u, kWeylB = 0xBB67AE85u;
+                                                 uint32_t c3, const PhiloxKeys& key) {
 #pragma unroll
   for (int round = 0; round < 10; ++round) {
-    const uint64_t pa = static_cast<uint64_t>(kMulA) * c0;
-    const uint64_t pb = static_cast<uint64_t>(kMulB) * c2;
-    const uint32_t n0 = static_cast<uint32_t>(pb >> 32) ^ c1 ^ k0;
-    const uint32_t n2 = static_cast<uint32_t>(pa >> 32) ^ c3 ^ k1;
+    const uint64_t pa = static_cast<uint64_t>(kPhiloxMulA) * c0;
+    const uint64_t pb = static_cast<uint64_t>(kPhiloxMulB) * c2;
+    const uint32_t n0 = static_cast<uint32_t>(pb >> 32) ^ c1 ^ key.k0[round];
+    const uint32_t n2 = static_cast<uint32_t>(pa >> 32) ^ c3 ^ key.k1[round];
     c1 = static_cast<uint32_t>(pb);
     c3 = static_cast<uint32_t>(pa);
     c0 = n0;
     c2 = n2;
-    k0 += kWeylA;
-    k1 += kWeylB;
   }
   return Philox4{c0, c1, c2, c3};
 }

@@ -287,11 +287,10 @@ __global__ void __launch_bounds__(kRedThreads) backward_kernel(const BackwardPar
   }
 }
 
-__global__ void philox_kernel(const uint32_t* ctr, int64_t n, uint32_t k0, uint32_t k1,
-                              uint32_t* out) {
+__global__ void philox_kernel(const uint32_t* ctr, int64_t n, const PhiloxKeys key, uint32_t* out) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const Philox4 r = philox4x32_10(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3], k0, k1);
+    const Philox4 r = philox4x32_10(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3], key);
     out[4 * i] = r.x;
     out[4 * i + 1] = r.y;
     out[4 * i + 2] = r.z;
@@ -323,8 +322,7 @@ cudaError_t launch_philox(const uint32_t* ctr, int64_t n, uint64_t seed, uint32_
   const int threads = 256;
   int64_t blocks = (n + threads - 1) / threads;
   if (blocks > 4096) blocks = 4096;
-  philox_kernel<<<static_cast<int>(blocks), threads, 0, st>>>(
-      ctr, n, static_cast<uint32_t>(seed & 0xffffffffu), static_cast<uint32_t>(seed >> 32), out);
+  philox_kernel<<<static_cast<int>(blocks), threads, 0, st>>>(ctr, n, philox_round_keys(seed), out);
   return cudaGetLastError();
 }
 

@@ -34,22 +34,25 @@ template <typename Real>
 struct Arith;
 
 // FP32 form: 23-bit uniforms (exact in float, open interval), hardware
-// approximations for rsqrt, sin/cos and exp.  |S'| = 1 to about 1e-6.
+// approximations for rsqrt, sin/cos and 2^x.  |S'| = 1 to about 1e-6.
 template <>
 struct Arith<float> {
-  static __device__ __forceinline__ float uni(uint32_t r) {
-    return __uint2float_rn((r >> 8) | 1u) * 0x1p-24f;
+  // 1 + m 2^-23 with m the top 23 bits of r, built from the bits (no int->float
+  // conversion); the uniform is that minus (1 - 2^-24) = (2m + 1) 2^-24, exactly.
+  static __device__ __forceinline__ float one_plus(uint32_t r) {
+    return __uint_as_float(0x3f800000u | (r >> 9));
   }
+  static __device__ __forceinline__ float uni(uint32_t r) { return one_plus(r) - 0.99999994f; }
   // Trial direction uniform on the sphere: cos(theta) = 2u0 - 1, phi = 2 pi u1.
   static __device__ __forceinline__ void trial(uint32_t r0, uint32_t r1, float& x, float& y,
                                                float& z) {
-    z = fmaf(2.0f, uni(r0), -1.0f);
-    const float q = (1.0f - z) * (1.0f + z);
-    const float rad = q * rsqrtf(q);  // q > 0: z never reaches +-1
+    z = fmaf(2.0f, uni(r0), -1.0f);  // 2 u0 - 1, exact, never +-1
+    const float q = fmaf(-z, z, 1.0f);  // 1 - z^2 > 0
+    const float rad = q * rsqrtf(q);
     float s, c;
-    // phi - pi lies in (-pi, pi), where the hardware sin/cos are accurate;
-    // cos(phi) = -cos(phi - pi), sin(phi) = -sin(phi - pi).
-    __sincosf(6.28318530717958648f * (uni(r1) - 0.5f), &s, &c);
+    // phi - pi = 2 pi (u1 - 1/2) lies in (-pi, pi), where the hardware sin/cos
+    // are accurate; cos(phi) = -cos(phi - pi), sin(phi) = -sin(phi - pi).
+    __sincosf(fmaf(6.28318531f, one_plus(r1), -9.42477763f), &s, &c);
     x = -rad * c;
     y = -rad * s;
   }
@@ -67,8 +70,15 @@ struct Arith<float> {
                                                   float hz, float J, float hf) {
     return -J * (dx * hx + dy * hy + dz * hz) - hf * dz;
   }
-  static __device__ __forceinline__ bool accept(float dE, float beta, uint32_t r2) {
-    return dE <= 0.0f || uni(r2) < __expf(-beta * dE);
+  // accept when dE <= 0, else iff u < exp(-beta dE) = 2^(-beta log2(e) dE);
+  // blog2e = beta log2(e) is precomputed per path.
+  static __device__ __forceinline__ bool accept(float dE, float blog2e, uint32_t r2) {
+    float p;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(p) : "f"(-blog2e * dE));
+    return dE <= 0.0f || uni(r2) < p;
+  }
+  static __device__ __forceinline__ float beta_param(double beta) {
+    return static_cast<float>(beta * 1.4426950408889634);
   }
   static __device__ __forceinline__ float shfl(float v, int o) {
     return __shfl_xor_sync(0xffffffffu, v, o);
@@ -114,6 +124,7 @@ struct Arith<double> {
   static __device__ __forceinline__ bool accept(double dE, double beta, uint32_t r2) {
     return dE <= 0.0 || uni(r2) < exp(__dmul_rn(-beta, dE));
   }
+  static __device__ __forceinline__ double beta_param(double beta) { return beta; }
   static __device__ __forceinline__ double shfl(double v, int o) {
     return __shfl_xor_sync(0xffffffffu, v, o);
   }
@@ -123,6 +134,7 @@ struct Arith<double> {
 // Periodic simple cubic lattice with compile-time L (even).  site() returns
 // the site index of half index h in colour c and fills the half indices of
 // its neighbours in the other colour, in the fixed order +x, -x, +y, -y, +z, -z.
+// Half index h = hx + HL*y + HP*z with hx = x / 2.
 template <int L>
 struct GeomSC {
   static constexpr int N = L * L * L;
@@ -130,7 +142,9 @@ struct GeomSC {
   static constexpr int HL = L / 2;
   static constexpr int HP = L * L / 2;
   static constexpr int NNB = 6;
+  static constexpr bool kColumns = true;
   __device__ __forceinline__ int count(int) const { return NH; }
+  static __device__ __forceinline__ constexpr int stride() { return NH; }
   __device__ __forceinline__ int site(int h, int c, int* nb, int& nn) const {
     const int hx = h % HL;
     const int t = h / HL;
@@ -154,7 +168,10 @@ struct GeomSC {
 struct GeomChain {
   int N;
   static constexpr int NNB = 2;
+  static constexpr bool kColumns = false;
+  static constexpr int HP = 1;
   __device__ __forceinline__ int count(int c) const { return c == 0 ? (N + 1) >> 1 : N >> 1; }
+  __device__ __forceinline__ int stride() const { return (N + 1) >> 1; }
   __device__ __forceinline__ int site(int h, int c, int* nb, int& nn) const {
     const int i = 2 * h + c;
     nn = 0;
@@ -175,6 +192,101 @@ __device__ __forceinline__ void group_sync(int tp, int bar) {
   }
 }
 
+// ------------------------------------------------------- one attempt -----
+// Per-thread partial sums of the measurement of one sweep.
+template <typename Real>
+struct Partials {
+  Real eb, mx, my, mz;
+};
+
+// One Metropolis attempt at site i (half index hh of the colour array `own`)
+// with neighbour half indices nb[0..nn) in `oth` (component stride S).
+// Sec. 2.2: trial spin, energy change from the local field, Metropolis test.
+template <typename Real, int NNB, bool kMeas, bool kEnergy>
+__device__ __forceinline__ void attempt(uint32_t i, uint32_t sweep, uint32_t c2, uint32_t c3,
+                                        const PhiloxKeys& key, Real* own, const Real* oth, int S,
+                                        int hh, const int* nb, int nn, Real J, Real hf, Real bp,
+                                        int& accepted, Partials<Real>& part) {
+  using A = Arith<Real>;
+  const Philox4 r = philox4x32_10(i, sweep, c2, c3, key);
+  Real tx, ty, tz;
+  A::trial(r.x, r.y, tx, ty, tz);
+  const Real ax = own[hh], ay = own[S + hh], az = own[2 * S + hh];
+  Real hx = Real(0), hy = Real(0), hz = Real(0);
+#pragma unroll
+  for (int j = 0; j < NNB; ++j) {
+    if (j < nn) {
+      hx = A::add(hx, oth[nb[j]]);
+      hy = A::add(hy, oth[S + nb[j]]);
+      hz = A::add(hz, oth[2 * S + nb[j]]);
+    }
+  }
+  const Real dE = A::delta_e(tx - ax, ty - ay, tz - az, hx, hy, hz, J, hf);
+  Real nx = ax, ny = ay, nz = az;
+  if (A::accept(dE, bp, r.z)) {
+    own[hh] = tx;
+    own[S + hh] = ty;
+    own[2 * S + hh] = tz;
+    nx = tx;
+    ny = ty;
+    nz = tz;
+    ++accepted;
+  }
+  if (kMeas) {
+    part.mx += nx;
+    part.my += ny;
+    part.mz += nz;
+    if (kEnergy) part.eb += nx * hx + ny * hy + nz * hz;
+  }
+}
+
+// One half-sweep of one thread: every site of colour c it owns.
+//
+// Column walk (simple cubic, tp a multiple of the HP half-sites of a z-plane):
+// the thread keeps its column (hx, y) and steps z by tp / HP, so its x and y
+// neighbour offsets are fixed and only the z wrap is decided per site.
+// Otherwise every site is decoded from its half index.
+template <typename Real, class Geom, bool kMeas>
+__device__ __forceinline__ void half_sweep(const Geom& geo, int c, uint32_t sweep, uint32_t c2,
+                                           uint32_t c3, const PhiloxKeys& key, Real* sp, int tid,
+                                           int tp, bool columns, Real J, Real hf, Real bp,
+                                           int& accepted, Partials<Real>& part) {
+  const int S = geo.stride();
+  Real* own = sp + c * 3 * S;
+  const Real* oth = sp + (1 - c) * 3 * S;
+  if constexpr (Geom::kColumns) {
+    if (columns) {
+      constexpr int HL = Geom::HL, HP = Geom::HP, LL = 2 * Geom::HL;
+      const int hx = tid % HL;
+      const int t = tid / HL;
+      const int y = t % LL;
+      const int dz = tp / HP;
+      const int oyp = (y == LL - 1) ? -(LL - 1) * HL : HL;
+      const int oym = (y == 0) ? (LL - 1) * HL : -HL;
+      const int oxp1 = (hx == HL - 1) ? -(HL - 1) : 1;  // +x offset when x is odd
+      const int oxm0 = (hx == 0) ? (HL - 1) : -1;         // -x offset when x is even
+      int z = t / LL;
+      for (int hh = tid; hh < Geom::NH; hh += tp, z += dz) {
+        const int p = (y + z + c) & 1;
+        const int nb[6] = {hh + (p ? oxp1 : 0), hh + (p ? 0 : oxm0), hh + oyp, hh + oym,
+                           (z == LL - 1) ? hh - (LL - 1) * HP : hh + HP,
+                           (z == 0) ? hh + (LL - 1) * HP : hh - HP};
+        attempt<Real, 6, kMeas, true>(static_cast<uint32_t>(2 * hh + p), sweep, c2, c3, key, own,
+                                      oth, S, hh, nb, 6, J, hf, bp, accepted, part);
+      }
+      return;
+    }
+  }
+  const int cnt = geo.count(c);
+  for (int hh = tid; hh < cnt; hh += tp) {
+    int nb[Geom::NNB];
+    int nn;
+    const int i = geo.site(hh, c, nb, nn);
+    attempt<Real, Geom::NNB, kMeas, true>(static_cast<uint32_t>(i), sweep, c2, c3, key, own, oth, S,
+                                          hh, nb, nn, J, hf, bp, accepted, part);
+  }
+}
+
 // ------------------------------------------------------------- one path --
 template <typename Real, class Geom>
 __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, int sys_idx,
@@ -182,25 +294,26 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
                                          int tid, int tp, int bar) {
   using A = Arith<Real>;
   double* acc = reinterpret_cast<double*>(slice + slice_acc_offset());
-  double* red = reinterpret_cast<double*>(slice + slice_red_offset());
+  Real* red = reinterpret_cast<Real*>(slice + slice_red_offset());
   Real* sp = reinterpret_cast<Real*>(slice + slice_spin_offset(tp));
-  const int NHm = sy.NH;
+  const int S = geo.stride();
   const uint32_t c2 = static_cast<uint32_t>(path);
   const uint32_t c3u = kTagUpdate | (static_cast<uint32_t>(sys_idx) << 8);
   const uint32_t c3i = kTagInit | (static_cast<uint32_t>(sys_idx) << 8);
   const Real J = static_cast<Real>(sy.J), hf = static_cast<Real>(sy.h);
-  const Real beta = static_cast<Real>(sy.beta);
-  const int lane = tid & 31, warp = tid >> 5;
+  const Real bp = A::beta_param(sy.beta);
+  const int lane = tid & 31, warp = tid >> 5, nwarps = tp >> 5;
+  const bool columns = Geom::kColumns && (tp % Geom::HP) == 0;
 
   // Random initial state (Sec. 2.2), or the ordered start of Sec. 5.
   for (int c = 0; c < 2; ++c) {
-    Real* own = sp + c * 3 * NHm;
+    Real* own = sp + c * 3 * S;
     const int cnt = geo.count(c);
     for (int hh = tid; hh < cnt; hh += tp) {
       int nb[Geom::NNB];
       int nn;
       const int i = geo.site(hh, c, nb, nn);
-      const Philox4 r = philox4x32_10(static_cast<uint32_t>(i), 0u, c2, c3i, P.k0, P.k1);
+      const Philox4 r = philox4x32_10(static_cast<uint32_t>(i), 0u, c2, c3i, P.key);
       Real x, y, z;
       if (P.init_mode == MP_INIT_ORDERED) {
         x = Real(0);
@@ -212,125 +325,114 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
         A::trial(r.x, r.y, x, y, z);
       }
       own[hh] = x;
-      own[NHm + hh] = y;
-      own[2 * NHm + hh] = z;
+      own[S + hh] = y;
+      own[2 * S + hh] = z;
     }
   }
   if (tid < kAccDoubles) acc[tid] = 0.0;
   group_sync(tp, bar);
 
   int accepted = 0;
-  const int64_t S = P.n_therm + P.n_meas;
-  for (int64_t s = 0; s < S; ++s) {
-    const bool meas = s >= P.n_therm;
-    Real eb = Real(0), mx = Real(0), my = Real(0), mz = Real(0);
-#pragma unroll 1
-    for (int c = 0; c < 2; ++c) {
-      Real* own = sp + c * 3 * NHm;
-      const Real* oth = sp + (1 - c) * 3 * NHm;
-      const int cnt = geo.count(c);
-      for (int hh = tid; hh < cnt; hh += tp) {
-        int nb[Geom::NNB];
-        int nn;
-        const int i = geo.site(hh, c, nb, nn);
-        const Philox4 r =
-            philox4x32_10(static_cast<uint32_t>(i), static_cast<uint32_t>(s), c2, c3u, P.k0, P.k1);
-        Real tx, ty, tz;
-        A::trial(r.x, r.y, tx, ty, tz);
-        const Real ax = own[hh], ay = own[NHm + hh], az = own[2 * NHm + hh];
-        Real hx = Real(0), hy = Real(0), hz = Real(0);
-#pragma unroll
-        for (int j = 0; j < Geom::NNB; ++j) {
-          if (j < nn) {
-            hx = A::add(hx, oth[nb[j]]);
-            hy = A::add(hy, oth[NHm + nb[j]]);
-            hz = A::add(hz, oth[2 * NHm + nb[j]]);
-          }
-        }
-        const Real dE = A::delta_e(tx - ax, ty - ay, tz - az, hx, hy, hz, J, hf);
-        Real nx = ax, ny = ay, nz = az;
-        if (A::accept(dE, beta, r.z)) {
-          own[hh] = tx;
-          own[NHm + hh] = ty;
-          own[2 * NHm + hh] = tz;
-          nx = tx;
-          ny = ty;
-          nz = tz;
-          ++accepted;
-        }
-        if (meas) {
-          mx += nx;
-          my += ny;
-          mz += nz;
-          if (c == 1) eb += nx * hx + ny * hy + nz * hz;
-        }
-      }
-      if (c == 1 && meas) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          eb += A::shfl(eb, o);
-          mx += A::shfl(mx, o);
-          my += A::shfl(my, o);
-          mz += A::shfl(mz, o);
-        }
-        if (lane == 0) {
-          red[warp * kRedSlots + 0] = static_cast<double>(eb);
-          red[warp * kRedSlots + 1] = static_cast<double>(mx);
-          red[warp * kRedSlots + 2] = static_cast<double>(my);
-          red[warp * kRedSlots + 3] = static_cast<double>(mz);
-        }
-      }
+  const int64_t nsweeps = P.n_therm + P.n_meas;
+  const double invN = 1.0 / static_cast<double>(sy.N);
+  for (int64_t s = 0; s < nsweeps; ++s) {
+    const uint32_t sw = static_cast<uint32_t>(s);
+    Partials<Real> part{Real(0), Real(0), Real(0), Real(0)};
+    if (s < P.n_therm) {
+      half_sweep<Real, Geom, false>(geo, 0, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf, bp,
+                                    accepted, part);
       group_sync(tp, bar);
+      half_sweep<Real, Geom, false>(geo, 1, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf, bp,
+                                    accepted, part);
+      group_sync(tp, bar);
+      continue;
     }
-    if (meas && tid == 0) {
-      double E = 0.0, MX = 0.0, MY = 0.0, MZ = 0.0;
-      for (int w = 0; w < (tp >> 5); ++w) {
-        E += red[w * kRedSlots + 0];
-        MX += red[w * kRedSlots + 1];
-        MY += red[w * kRedSlots + 2];
-        MZ += red[w * kRedSlots + 3];
-      }
-      const double invN = 1.0 / static_cast<double>(sy.N);
-      const double e = (-sy.J * E - sy.h * MZ) * invN;
-      const double ex = MX * invN, ey = MY * invN, ez = MZ * invN;
-      const double m2 = ex * ex + ey * ey + ez * ez;
-      const double m = sqrt(m2);
-      acc[MP_R_E] += e;
-      acc[MP_R_E2] += e * e;
-      acc[MP_R_M] += m;
-      acc[MP_R_M2] += m2;
-      acc[MP_R_M4] += m2 * m2;
-      acc[MP_R_MX] += ex;
-      acc[MP_R_MY] += ey;
-      acc[MP_R_MZ] += ez;
-      acc[MP_R_MZ2] += ez * ez;
-      acc[MP_R_AMZ] += fabs(ez);
-      acc[MP_R_EM] += e * m;
-      acc[MP_R_EMZ] += e * ez;
-      acc[MP_R_MMZ] += m * ez;
-      if (s == S - 1) {
-        acc[MP_R_FMX] = ex;
-        acc[MP_R_FMY] = ey;
-        acc[MP_R_FMZ] = ez;
-        acc[MP_R_FE] = e;
-      }
+    // Measurement sweep.  Colour-0 sites keep their values during the colour-1
+    // pass, so the colour-1 local fields give every bond once.
+    half_sweep<Real, Geom, true>(geo, 0, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf, bp,
+                                 accepted, part);
+    part.eb = Real(0);
+    group_sync(tp, bar);
+    half_sweep<Real, Geom, true>(geo, 1, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf, bp,
+                                 accepted, part);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      part.eb += A::shfl(part.eb, o);
+      part.mx += A::shfl(part.mx, o);
+      part.my += A::shfl(part.my, o);
+      part.mz += A::shfl(part.mz, o);
     }
+    if (lane == 0) {
+      red[warp * kRedSlots + 0] = part.eb;
+      red[warp * kRedSlots + 1] = part.mx;
+      red[warp * kRedSlots + 2] = part.my;
+      red[warp * kRedSlots + 3] = part.mz;
+    }
+    group_sync(tp, bar);
+    if (warp == 0) {
+      // lane w brings warp w's partials; a shuffle tree gives every lane the
+      // totals; lane k then adds observable k to its FP64 accumulator.
+      Real E = Real(0), MX = Real(0), MY = Real(0), MZ = Real(0);
+      if (lane < nwarps) {
+        E = red[lane * kRedSlots + 0];
+        MX = red[lane * kRedSlots + 1];
+        MY = red[lane * kRedSlots + 2];
+        MZ = red[lane * kRedSlots + 3];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        E += A::shfl(E, o);
+        MX += A::shfl(MX, o);
+        MY += A::shfl(MY, o);
+        MZ += A::shfl(MZ, o);
+      }
+      const Real rN = static_cast<Real>(invN);
+      const Real e = (-J * E - hf * MZ) * rN;
+      const Real ex = MX * rN, ey = MY * rN, ez = MZ * rN;
+      const Real m2 = ex * ex + ey * ey + ez * ez;
+      const Real m = sqrt(m2);
+      Real v = Real(0);
+      switch (lane) {
+        case MP_R_E: v = e; break;
+        case MP_R_E2: v = e * e; break;
+        case MP_R_M: v = m; break;
+        case MP_R_M2: v = m2; break;
+        case MP_R_M4: v = m2 * m2; break;
+        case MP_R_MX: v = ex; break;
+        case MP_R_MY: v = ey; break;
+        case MP_R_MZ: v = ez; break;
+        case MP_R_MZ2: v = ez * ez; break;
+        case MP_R_AMZ: v = fabs(ez); break;
+        case MP_R_EM: v = e * m; break;
+        case MP_R_EMZ: v = e * ez; break;
+        case MP_R_MMZ: v = m * ez; break;
+        case MP_R_FMX: v = ex; break;
+        case MP_R_FMY: v = ey; break;
+        case MP_R_FMZ: v = ez; break;
+        case MP_R_FE: v = e; break;
+        default: break;
+      }
+      if (lane <= MP_R_MMZ) acc[lane] += static_cast<double>(v);
+      else if (lane <= MP_R_FE && s == nsweeps - 1) acc[lane] = static_cast<double>(v);
+    }
+    // red[] is rewritten only after the next colour-0 barrier, which warp 0
+    // reaches after reading it.
   }
 
   // Final state: acceptance count and the worst | |S| - 1 |, reduced over the group.
-  double worst = 0.0;
+  Real worst = Real(0);
   for (int c = 0; c < 2; ++c) {
-    const Real* own = sp + c * 3 * NHm;
+    const Real* own = sp + c * 3 * S;
     for (int hh = tid; hh < geo.count(c); hh += tp) {
-      const double x = own[hh], y = own[NHm + hh], z = own[2 * NHm + hh];
-      worst = fmax(worst, fabs(sqrt(x * x + y * y + z * z) - 1.0));
+      const Real x = own[hh], y = own[S + hh], z = own[2 * S + hh];
+      worst = fmax(worst, fabs(sqrt(x * x + y * y + z * z) - Real(1)));
     }
   }
-  double nacc = static_cast<double>(accepted);
+  Real nacc = static_cast<Real>(accepted);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    nacc += __shfl_xor_sync(0xffffffffu, nacc, o);
-    worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+    nacc += A::shfl(nacc, o);
+    worst = fmax(worst, A::shfl(worst, o));
   }
   if (lane == 0) {
     red[warp * kRedSlots + 0] = nacc;
@@ -339,29 +441,29 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
   group_sync(tp, bar);
   if (tid == 0) {
     double tot = 0.0, wmax = 0.0;
-    for (int w = 0; w < (tp >> 5); ++w) {
-      tot += red[w * kRedSlots + 0];
-      wmax = fmax(wmax, red[w * kRedSlots + 1]);
+    for (int w = 0; w < nwarps; ++w) {
+      tot += static_cast<double>(red[w * kRedSlots + 0]);
+      wmax = fmax(wmax, static_cast<double>(red[w * kRedSlots + 1]));
     }
     double* rec = P.records + (sy.rec_offset + path) * MP_NREC;
     const double inv = 1.0 / static_cast<double>(P.n_meas);
     for (int k = MP_R_E; k <= MP_R_MMZ; ++k) rec[k] = acc[k] * inv;
     for (int k = MP_R_FMX; k <= MP_R_FE; ++k) rec[k] = acc[k];
-    rec[MP_R_ACC] = tot / (static_cast<double>(S) * static_cast<double>(sy.N));
+    rec[MP_R_ACC] = tot / (static_cast<double>(nsweeps) * static_cast<double>(sy.N));
     rec[MP_R_NORM] = wmax;
     rec[MP_R_SPARE] = 0.0;
   }
   if (P.spins != nullptr) {
     double* out = P.spins + P.spin_offset[sys_idx] + path * 3 * static_cast<int64_t>(sy.N);
     for (int c = 0; c < 2; ++c) {
-      const Real* own = sp + c * 3 * NHm;
+      const Real* own = sp + c * 3 * S;
       for (int hh = tid; hh < geo.count(c); hh += tp) {
         int nb[Geom::NNB];
         int nn;
         const int i = geo.site(hh, c, nb, nn);
         out[3 * i + 0] = own[hh];
-        out[3 * i + 1] = own[NHm + hh];
-        out[3 * i + 2] = own[2 * NHm + hh];
+        out[3 * i + 1] = own[S + hh];
+        out[3 * i + 2] = own[2 * S + hh];
       }
     }
   }
@@ -373,7 +475,13 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
 #define MPK_FOR_EACH_L_FP32(X) X(2) X(4) X(6) X(8) X(10) X(12) X(14) X(16) X(18) X(20) X(22) X(24) X(26)
 #define MPK_FOR_EACH_L_FP64(X) X(2) X(4) X(6) X(8) X(10) X(12) X(14) X(16) X(18) X(20)
 
-template <typename Real>
+// Kernel variants: kLattice > 0 runs only simple cubic L = kLattice (a batch of
+// one size), kLattice = kChainKernel only open chains, kLattice = kMixedKernel
+// switches on each work item's lattice (a batch of uneven sizes).
+constexpr int kMixedKernel = 0;
+constexpr int kChainKernel = -1;
+
+template <typename Real, int kLattice>
 __device__ __forceinline__ void dispatch_path(const DevSystem& sy, int sys_idx, int64_t path,
                                               const SweepParams& P, unsigned char* slice, int tid,
                                               int tp, int bar);
@@ -384,7 +492,7 @@ struct CtaLimit {
   static constexpr int value = sizeof(Real) == 8 ? 512 : kMaxCta;
 };
 
-template <typename Real>
+template <typename Real, int kLattice>
 __global__ void __launch_bounds__(CtaLimit<Real>::value, 1) sweep_kernel(const SweepParams P) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_item;
@@ -399,7 +507,8 @@ __global__ void __launch_bounds__(CtaLimit<Real>::value, 1) sweep_kernel(const S
     const int g = static_cast<int>(threadIdx.x) / sy.tp;
     const int tid = static_cast<int>(threadIdx.x) - g * sy.tp;
     if (g < it.count) {
-      dispatch_path<Real>(sy, it.sys, it.path0 + g, P, smem + g * sy.slice_bytes, tid, sy.tp, 1 + g);
+      dispatch_path<Real, kLattice>(sy, it.sys, it.path0 + g, P, smem + g * sy.slice_bytes, tid,
+                                    sy.tp, 1 + g);
     }
   }
 }

@@ -1,53 +1,81 @@
 // FP32 form of the shared-memory sweep: FP32 spins, energy differences and
 // Boltzmann factors; FP64 per-path accumulators.
 #include "kernels.h"
+#define REAL float
+#define SUFFIX(f) f##_fp32
+#define MPK_FOR_EACH_L MPK_FOR_EACH_L_FP32
 #include "sweep.cuh"
 
 namespace mpk {
 
-template <>
-__device__ __forceinline__ void dispatch_path<float>(const DevSystem& sy, int sys_idx, int64_t path,
-                                                     const SweepParams& P, unsigned char* slice,
-                                                     int tid, int tp, int bar) {
-  if (sy.lattice == MP_LATTICE_CHAIN) {
-    run_path<float>(GeomChain{sy.N}, sy, sys_idx, path, P, slice, tid, tp, bar);
-    return;
-  }
-  switch (sy.L) {
-#define MPK_CASE(LL)                                                             \
-  case LL:                                                                       \
-    run_path<float>(GeomSC<LL>{}, sy, sys_idx, path, P, slice, tid, tp, bar);    \
+template <typename Real, int kLattice>
+__device__ __forceinline__ void dispatch_path(const DevSystem& sy, int sys_idx, int64_t path,
+                                              const SweepParams& P, unsigned char* slice, int tid,
+                                              int tp, int bar) {
+  if constexpr (kLattice > 0) {
+    run_path<Real>(GeomSC<kLattice>{}, sy, sys_idx, path, P, slice, tid, tp, bar);
+  } else if constexpr (kLattice == kChainKernel) {
+    run_path<Real>(GeomChain{sy.N}, sy, sys_idx, path, P, slice, tid, tp, bar);
+  } else {
+    if (sy.lattice == MP_LATTICE_CHAIN) {
+      run_path<Real>(GeomChain{sy.N}, sy, sys_idx, path, P, slice, tid, tp, bar);
+      return;
+    }
+    switch (sy.L) {
+#define MPK_CASE(LL)                                                           \
+  case LL:                                                                     \
+    run_path<Real>(GeomSC<LL>{}, sy, sys_idx, path, P, slice, tid, tp, bar);   \
     break;
-    MPK_FOR_EACH_L_FP32(MPK_CASE)
+      MPK_FOR_EACH_L(MPK_CASE)
 #undef MPK_CASE
-    default:
-      break;
+      default:
+        break;
+    }
   }
 }
 
-bool sweep_supports_L_fp32(int L) {
-  switch (L) {
-#define MPK_CASE(LL) case LL:
-    MPK_FOR_EACH_L_FP32(MPK_CASE)
+// kernel of a variant (simple cubic L, chain, or mixed); nullptr if not built
+static const void* kernel_of(int variant) {
+  switch (variant) {
+    case kMixedKernel: return reinterpret_cast<const void*>(sweep_kernel<REAL, kMixedKernel>);
+    case kChainKernel: return reinterpret_cast<const void*>(sweep_kernel<REAL, kChainKernel>);
+#define MPK_CASE(LL) \
+    case LL: return reinterpret_cast<const void*>(sweep_kernel<REAL, LL>);
+      MPK_FOR_EACH_L(MPK_CASE)
 #undef MPK_CASE
-    return true;
-    default:
-      return false;
+    default: return nullptr;
   }
 }
 
-cudaError_t sweep_prepare_fp32() {
-  return cudaFuncSetAttribute(sweep_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              kSmemMax);
+bool SUFFIX(sweep_supports_L)(int L) { return L > 0 && kernel_of(L) != nullptr; }
+
+// Raises a variant's dynamic shared-memory limit to what the device allows
+// beside the kernel's static shared memory; returns that limit in *max_dynamic.
+cudaError_t SUFFIX(sweep_prepare)(int variant, int device, int* max_dynamic) {
+  const void* k = kernel_of(variant);
+  if (!k) return cudaErrorInvalidValue;
+  int optin = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, k);
+  if (e != cudaSuccess) return e;
+  *max_dynamic = optin - static_cast<int>(fa.sharedSizeBytes);
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, *max_dynamic);
 }
 
-cudaError_t sweep_occupancy_fp32(int cta, int smem, int* blocks) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, sweep_kernel<float>, cta, smem);
+cudaError_t SUFFIX(sweep_occupancy)(int variant, int cta, int smem, int* blocks) {
+  const void* k = kernel_of(variant);
+  if (!k) return cudaErrorInvalidValue;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, cta, smem);
 }
 
-cudaError_t launch_sweep_fp32(const SweepParams& p, int grid, int cta, int smem, cudaStream_t st) {
-  sweep_kernel<float><<<grid, cta, smem, st>>>(p);
-  return cudaGetLastError();
+cudaError_t SUFFIX(launch_sweep)(int variant, const SweepParams& p, int grid, int cta, int smem,
+                                 cudaStream_t st) {
+  const void* k = kernel_of(variant);
+  if (!k) return cudaErrorInvalidValue;
+  void* args[] = {const_cast<SweepParams*>(&p)};
+  return cudaLaunchKernel(k, dim3(grid), dim3(cta), args, static_cast<size_t>(smem), st);
 }
 
 }  // namespace mpk
