@@ -24,7 +24,7 @@ struct DevSystem {
   int32_t tp;           // threads per path (multiple of 32)
   int32_t g;            // paths per CTA
   int32_t slice_bytes;  // shared memory per path
-  int32_t pad;
+  int32_t ring;         // measurement sweeps per half of the partial-sum ring
   double T, J, h, beta;
   int64_t rec_offset;   // global index of this system's path 0
   int64_t n_paths;
@@ -52,10 +52,13 @@ struct SweepParams {
 };
 
 // Byte offsets inside one path's shared-memory slice.
+// [acc: FP64 accumulators][ring: 2 x R sweeps x warps x kRedSlots partials][spins]
+// (ring elements are sized 8 bytes, enough for either precision and for the
+// two doubles per warp of the final reduction)
 __host__ __device__ constexpr int slice_acc_offset() { return 0; }
 __host__ __device__ constexpr int slice_red_offset() { return kAccDoubles * 8; }
-__host__ __device__ inline int slice_spin_offset(int tp) {
-  return kAccDoubles * 8 + ((tp / 32) * kRedSlots * 8 + 127) / 128 * 128;
+__host__ __device__ inline int slice_spin_offset(int tp, int ring) {
+  return kAccDoubles * 8 + (2 * ring * (tp / 32) * kRedSlots * 8 + 127) / 128 * 128;
 }
 
 }  // namespace mpk

@@ -29,7 +29,8 @@ struct BackwardParams {
 // of simple cubic lattices of that one size, -1 open chains only, 0 a batch
 // of uneven sizes (the kernel switches per work item).
 bool sweep_supports_L(int precision, int L);
-cudaError_t sweep_prepare(int precision, int variant, int device, int* max_dynamic);
+cudaError_t sweep_prepare(int precision, int variant, int device, int* max_dynamic,
+                          int* max_threads);
 cudaError_t sweep_occupancy(int precision, int variant, int cta, int smem, int* blocks_per_sm);
 cudaError_t launch_sweep(int precision, int variant, const SweepParams& p, int grid, int cta,
                          int smem, cudaStream_t st);

@@ -22,8 +22,8 @@ namespace mpk {
 
 bool sweep_supports_L_fp32(int L);
 bool sweep_supports_L_fp64(int L);
-cudaError_t sweep_prepare_fp32(int variant, int device, int* max_dynamic);
-cudaError_t sweep_prepare_fp64(int variant, int device, int* max_dynamic);
+cudaError_t sweep_prepare_fp32(int variant, int device, int* max_dynamic, int* max_threads);
+cudaError_t sweep_prepare_fp64(int variant, int device, int* max_dynamic, int* max_threads);
 cudaError_t sweep_occupancy_fp32(int variant, int cta, int smem, int* blocks);
 cudaError_t sweep_occupancy_fp64(int variant, int cta, int smem, int* blocks);
 cudaError_t launch_sweep_fp32(int variant, const SweepParams& p, int grid, int cta, int smem,
@@ -34,9 +34,10 @@ cudaError_t launch_sweep_fp64(int variant, const SweepParams& p, int grid, int c
 bool sweep_supports_L(int precision, int L) {
   return precision == MP_FP64 ? sweep_supports_L_fp64(L) : sweep_supports_L_fp32(L);
 }
-cudaError_t sweep_prepare(int precision, int variant, int device, int* max_dynamic) {
-  return precision == MP_FP64 ? sweep_prepare_fp64(variant, device, max_dynamic)
-                              : sweep_prepare_fp32(variant, device, max_dynamic);
+cudaError_t sweep_prepare(int precision, int variant, int device, int* max_dynamic,
+                          int* max_threads) {
+  return precision == MP_FP64 ? sweep_prepare_fp64(variant, device, max_dynamic, max_threads)
+                              : sweep_prepare_fp32(variant, device, max_dynamic, max_threads);
 }
 cudaError_t sweep_occupancy(int precision, int variant, int cta, int smem, int* blocks) {
   return precision == MP_FP64 ? sweep_occupancy_fp64(variant, cta, smem, blocks)
@@ -210,7 +211,6 @@ int validate(const mp_config* cfg) {
 // items to cover every SM twice.
 int plan(mp_state* h, const mp_config* cfg) {
   const int real = h->precision == MP_FP64 ? 8 : 4;
-  const int cta_max = h->precision == MP_FP64 ? 512 : kMaxCta;  // CtaLimit of the sweep kernel
   const int n = static_cast<int>(h->systems.size());
   // one kernel per lattice size when the batch has a single size
   int variant = h->systems[0].lattice == MP_LATTICE_CHAIN ? -1 : h->systems[0].L;
@@ -219,11 +219,13 @@ int plan(mp_state* h, const mp_config* cfg) {
     if (v != variant) variant = 0;
   }
   h->variant = variant;
-  int sms = 0, smem_max = 0;
+  int sms = 0, smem_max = 0, cta_max = 0;
   MP_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-  MP_CUDA(h, sweep_prepare(h->precision, variant, h->device, &smem_max));
+  MP_CUDA(h, sweep_prepare(h->precision, variant, h->device, &smem_max, &cta_max));
+  // kernels with room for more registers per thread take more sites per thread
+  const double target = cta_max <= 512 ? 16.0 : 8.0;
   MP_CUDA(h, reduce_prepare());
-  std::vector<int> tp(n), slice(n);
+  std::vector<int> tp(n), slice(n), ring(n);
   int max_tp = 32;
   for (int k = 0; k < n; ++k) {
     const int64_t N = sites_of(h->systems[k]);
@@ -236,17 +238,24 @@ int plan(mp_state* h, const mp_config* cfg) {
       double best = 1e30;
       for (int c = HP; c <= std::min(cta_max, round_up(NH, 32)); c += HP) {
         if (c % 32) continue;
-        const double d = std::fabs(static_cast<double>(NH) / c - 8.0);
+        const double d = std::fabs(static_cast<double>(NH) / c - target);
         if (d < best) {
           best = d;
           t = c;
         }
       }
     }
-    if (t == 0) t = std::min(cta_max, std::max(32, round_up((NH + 7) / 8, 32)));
+    if (t == 0)
+      t = std::min(cta_max, std::max(32, round_up(static_cast<int>(std::ceil(NH / target)), 32)));
     if (t > cta_max) return fail(h, MP_EINVAL, "threads_per_path %d above %d", t, cta_max);
     tp[k] = t;
-    slice[k] = round_up(slice_spin_offset(t) + 6 * NH * real, 128);
+    // partial-sum ring: the largest power of two up to 16 sweeps that fits
+    ring[k] = 16;
+    slice[k] = round_up(slice_spin_offset(t, ring[k]) + 6 * NH * real, 128);
+    while (ring[k] > 1 && slice[k] > smem_max) {
+      ring[k] /= 2;
+      slice[k] = round_up(slice_spin_offset(t, ring[k]) + 6 * NH * real, 128);
+    }
     if (slice[k] > smem_max)
       return fail(h, MP_EINVAL, "system %d needs %d bytes of shared memory per path (max %d)", k,
                   slice[k], smem_max);
@@ -290,7 +299,7 @@ int plan(mp_state* h, const mp_config* cfg) {
     d.tp = tp[k];
     d.g = paths_per_cta(k, cta);
     d.slice_bytes = slice[k];
-    d.pad = 0;
+    d.ring = ring[k];
     d.T = s.T;
     d.J = s.J;
     d.h = s.h;

@@ -199,28 +199,19 @@ struct Partials {
   Real eb, mx, my, mz;
 };
 
-// One Metropolis attempt at site i (half index hh of the colour array `own`)
-// with neighbour half indices nb[0..nn) in `oth` (component stride S).
-// Sec. 2.2: trial spin, energy change from the local field, Metropolis test.
-template <typename Real, int NNB, bool kMeas, bool kEnergy>
-__device__ __forceinline__ void attempt(uint32_t i, uint32_t sweep, uint32_t c2, uint32_t c3,
-                                        const PhiloxKeys& key, Real* own, const Real* oth, int S,
-                                        int hh, const int* nb, int nn, Real J, Real hf, Real bp,
-                                        int& accepted, Partials<Real>& part) {
+// The Metropolis step at site i (half index hh of the colour array `own`,
+// component stride S) given its local field (hx, hy, hz), Sec. 2.2: trial
+// spin, energy change from the local field, acceptance test.
+template <typename Real, bool kMeas, bool kEnergy>
+__device__ __forceinline__ void update(uint32_t i, uint32_t sweep, uint32_t c2, uint32_t c3,
+                                       const PhiloxKeys& key, Real* own, int S, int hh, Real hx,
+                                       Real hy, Real hz, Real J, Real hf, Real bp, int& accepted,
+                                       Partials<Real>& part) {
   using A = Arith<Real>;
   const Philox4 r = philox4x32_10(i, sweep, c2, c3, key);
   Real tx, ty, tz;
   A::trial(r.x, r.y, tx, ty, tz);
   const Real ax = own[hh], ay = own[S + hh], az = own[2 * S + hh];
-  Real hx = Real(0), hy = Real(0), hz = Real(0);
-#pragma unroll
-  for (int j = 0; j < NNB; ++j) {
-    if (j < nn) {
-      hx = A::add(hx, oth[nb[j]]);
-      hy = A::add(hy, oth[S + nb[j]]);
-      hz = A::add(hz, oth[2 * S + nb[j]]);
-    }
-  }
   const Real dE = A::delta_e(tx - ax, ty - ay, tz - az, hx, hy, hz, J, hf);
   Real nx = ax, ny = ay, nz = az;
   if (A::accept(dE, bp, r.z)) {
@@ -240,13 +231,40 @@ __device__ __forceinline__ void attempt(uint32_t i, uint32_t sweep, uint32_t c2,
   }
 }
 
+// One Metropolis attempt with the neighbours' half indices nb[0..nn) in `oth`,
+// summed in the fixed order nb[0], nb[1], ...
+template <typename Real, int NNB, bool kMeas, bool kEnergy>
+__device__ __forceinline__ void attempt(uint32_t i, uint32_t sweep, uint32_t c2, uint32_t c3,
+                                        const PhiloxKeys& key, Real* own, const Real* oth, int S,
+                                        int hh, const int* nb, int nn, Real J, Real hf, Real bp,
+                                        int& accepted, Partials<Real>& part) {
+  using A = Arith<Real>;
+  Real hx = Real(0), hy = Real(0), hz = Real(0);
+#pragma unroll
+  for (int j = 0; j < NNB; ++j) {
+    if (j < nn) {
+      hx = A::add(hx, oth[nb[j]]);
+      hy = A::add(hy, oth[S + nb[j]]);
+      hz = A::add(hz, oth[2 * S + nb[j]]);
+    }
+  }
+  update<Real, kMeas, kEnergy>(i, sweep, c2, c3, key, own, S, hh, hx, hy, hz, J, hf, bp, accepted,
+                               part);
+}
+
+// Sites of a column interleaved by the compiler (independent Philox chains):
+// 4 in the FP32 kernels with 128 registers per thread (L <= 16), 2 in those
+// with 64.
+template <typename Real, int L>
+constexpr int kColumnUnroll = sizeof(Real) == 8 ? 1 : (L <= 16 ? 4 : 2);
+
 // One half-sweep of one thread: every site of colour c it owns.
 //
 // Column walk (simple cubic, tp a multiple of the HP half-sites of a z-plane):
 // the thread keeps its column (hx, y) and steps z by tp / HP, so its x and y
 // neighbour offsets are fixed and only the z wrap is decided per site.
 // Otherwise every site is decoded from its half index.
-template <typename Real, class Geom, bool kMeas>
+template <typename Real, class Geom, bool kMeas, bool kEnergy>
 __device__ __forceinline__ void half_sweep(const Geom& geo, int c, uint32_t sweep, uint32_t c2,
                                            uint32_t c3, const PhiloxKeys& key, Real* sp, int tid,
                                            int tp, bool columns, Real J, Real hf, Real bp,
@@ -266,13 +284,37 @@ __device__ __forceinline__ void half_sweep(const Geom& geo, int c, uint32_t swee
       const int oxp1 = (hx == HL - 1) ? -(HL - 1) : 1;  // +x offset when x is odd
       const int oxm0 = (hx == 0) ? (HL - 1) : -1;         // -x offset when x is even
       int z = t / LL;
+      // With dz = 2 the +z neighbour of one site of the column is the -z
+      // neighbour of the next: it is loaded once.
+      Real czx = Real(0), czy = Real(0), czz = Real(0);
+#pragma unroll(kColumnUnroll<Real, LL>)
       for (int hh = tid; hh < Geom::NH; hh += tp, z += dz) {
         const int p = (y + z + c) & 1;
-        const int nb[6] = {hh + (p ? oxp1 : 0), hh + (p ? 0 : oxm0), hh + oyp, hh + oym,
-                           (z == LL - 1) ? hh - (LL - 1) * HP : hh + HP,
-                           (z == 0) ? hh + (LL - 1) * HP : hh - HP};
-        attempt<Real, 6, kMeas, true>(static_cast<uint32_t>(2 * hh + p), sweep, c2, c3, key, own,
-                                      oth, S, hh, nb, 6, J, hf, bp, accepted, part);
+        const int n0 = hh + (p ? oxp1 : 0), n1 = hh + (p ? 0 : oxm0);
+        const int n2 = hh + oyp, n3 = hh + oym;
+        const int n4 = (z == LL - 1) ? hh - (LL - 1) * HP : hh + HP;
+        Real mzx, mzy, mzz;
+        if (dz == 2 && hh != tid) {
+          mzx = czx;
+          mzy = czy;
+          mzz = czz;
+        } else {
+          const int n5 = (z == 0) ? hh + (LL - 1) * HP : hh - HP;
+          mzx = oth[n5];
+          mzy = oth[S + n5];
+          mzz = oth[2 * S + n5];
+        }
+        czx = oth[n4];
+        czy = oth[S + n4];
+        czz = oth[2 * S + n4];
+        using A = Arith<Real>;
+        Real hx = A::add(A::add(A::add(A::add(A::add(oth[n0], oth[n1]), oth[n2]), oth[n3]), czx), mzx);
+        Real hy = A::add(A::add(A::add(A::add(A::add(oth[S + n0], oth[S + n1]), oth[S + n2]),
+                                              oth[S + n3]), czy), mzy);
+        Real hz = A::add(A::add(A::add(A::add(A::add(oth[2 * S + n0], oth[2 * S + n1]),
+                                                     oth[2 * S + n2]), oth[2 * S + n3]), czz), mzz);
+        update<Real, kMeas, kEnergy>(static_cast<uint32_t>(2 * hh + p), sweep, c2, c3, key, own, S,
+                                     hh, hx, hy, hz, J, hf, bp, accepted, part);
       }
       return;
     }
@@ -282,8 +324,8 @@ __device__ __forceinline__ void half_sweep(const Geom& geo, int c, uint32_t swee
     int nb[Geom::NNB];
     int nn;
     const int i = geo.site(hh, c, nb, nn);
-    attempt<Real, Geom::NNB, kMeas, true>(static_cast<uint32_t>(i), sweep, c2, c3, key, own, oth, S,
-                                          hh, nb, nn, J, hf, bp, accepted, part);
+    attempt<Real, Geom::NNB, kMeas, kEnergy>(static_cast<uint32_t>(i), sweep, c2, c3, key, own, oth,
+                                             S, hh, nb, nn, J, hf, bp, accepted, part);
   }
 }
 
@@ -295,7 +337,7 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
   using A = Arith<Real>;
   double* acc = reinterpret_cast<double*>(slice + slice_acc_offset());
   Real* red = reinterpret_cast<Real*>(slice + slice_red_offset());
-  Real* sp = reinterpret_cast<Real*>(slice + slice_spin_offset(tp));
+  Real* sp = reinterpret_cast<Real*>(slice + slice_spin_offset(tp, sy.ring));
   const int S = geo.stride();
   const uint32_t c2 = static_cast<uint32_t>(path);
   const uint32_t c3u = kTagUpdate | (static_cast<uint32_t>(sys_idx) << 8);
@@ -335,64 +377,40 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
   int accepted = 0;
   const int64_t nsweeps = P.n_therm + P.n_meas;
   const double invN = 1.0 / static_cast<double>(sy.N);
-  for (int64_t s = 0; s < nsweeps; ++s) {
-    const uint32_t sw = static_cast<uint32_t>(s);
-    Partials<Real> part{Real(0), Real(0), Real(0), Real(0)};
-    if (s < P.n_therm) {
-      half_sweep<Real, Geom, false>(geo, 0, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf, bp,
-                                    accepted, part);
-      group_sync(tp, bar);
-      half_sweep<Real, Geom, false>(geo, 1, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf, bp,
-                                    accepted, part);
-      group_sync(tp, bar);
-      continue;
+  const int R = sy.ring;  // measurement sweeps per ring half
+  // ring[half][slot][warp][4]: each warp's partial sums (E_bond, Mx, My, Mz)
+  // of one measurement sweep.  A half of R sweeps is flushed into the FP64
+  // accumulators by all warps together after the next barrier, while the
+  // other half fills.
+  auto slot_ptr = [&](int64_t j) {
+    return red + ((((j / R) & 1) * R + (j % R)) * nwarps) * kRedSlots;
+  };
+  // Per-site observables (Sec. 2.2) of one measurement sweep from its slot.
+  auto observe = [&](const Real* sl, Real& e, Real& ex, Real& ey, Real& ez) {
+    Real E = Real(0), MX = Real(0), MY = Real(0), MZ = Real(0);
+    for (int w = 0; w < nwarps; ++w) {
+      E += sl[w * kRedSlots + 0];
+      MX += sl[w * kRedSlots + 1];
+      MY += sl[w * kRedSlots + 2];
+      MZ += sl[w * kRedSlots + 3];
     }
-    // Measurement sweep.  Colour-0 sites keep their values during the colour-1
-    // pass, so the colour-1 local fields give every bond once.
-    half_sweep<Real, Geom, true>(geo, 0, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf, bp,
-                                 accepted, part);
-    part.eb = Real(0);
-    group_sync(tp, bar);
-    half_sweep<Real, Geom, true>(geo, 1, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf, bp,
-                                 accepted, part);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      part.eb += A::shfl(part.eb, o);
-      part.mx += A::shfl(part.mx, o);
-      part.my += A::shfl(part.my, o);
-      part.mz += A::shfl(part.mz, o);
-    }
-    if (lane == 0) {
-      red[warp * kRedSlots + 0] = part.eb;
-      red[warp * kRedSlots + 1] = part.mx;
-      red[warp * kRedSlots + 2] = part.my;
-      red[warp * kRedSlots + 3] = part.mz;
-    }
-    group_sync(tp, bar);
-    if (warp == 0) {
-      // lane w brings warp w's partials; a shuffle tree gives every lane the
-      // totals; lane k then adds observable k to its FP64 accumulator.
-      Real E = Real(0), MX = Real(0), MY = Real(0), MZ = Real(0);
-      if (lane < nwarps) {
-        E = red[lane * kRedSlots + 0];
-        MX = red[lane * kRedSlots + 1];
-        MY = red[lane * kRedSlots + 2];
-        MZ = red[lane * kRedSlots + 3];
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        E += A::shfl(E, o);
-        MX += A::shfl(MX, o);
-        MY += A::shfl(MY, o);
-        MZ += A::shfl(MZ, o);
-      }
-      const Real rN = static_cast<Real>(invN);
-      const Real e = (-J * E - hf * MZ) * rN;
-      const Real ex = MX * rN, ey = MY * rN, ez = MZ * rN;
-      const Real m2 = ex * ex + ey * ey + ez * ez;
-      const Real m = sqrt(m2);
-      Real v = Real(0);
-      switch (lane) {
+    const Real rN = static_cast<Real>(invN);
+    e = (-J * E - hf * MZ) * rN;
+    ex = MX * rN;
+    ey = MY * rN;
+    ez = MZ * rN;
+  };
+  // Flush measurement sweeps j0 .. j0+n-1 (one ring half): lane l takes
+  // sweep j0+l; warp w owns observables w, w + warps, ...; each owned
+  // observable is summed over the lanes and added to its FP64 accumulator.
+  auto flush = [&](int64_t j0, int n) {
+    Real e = Real(0), ex = Real(0), ey = Real(0), ez = Real(0);
+    if (lane < n) observe(slot_ptr(j0 + lane), e, ex, ey, ez);
+    const Real m2 = ex * ex + ey * ey + ez * ez;
+    const Real m = sqrt(m2);
+    for (int k = warp; k <= MP_R_MMZ; k += nwarps) {
+      Real v;
+      switch (k) {  // k is the same in every lane of the warp
         case MP_R_E: v = e; break;
         case MP_R_E2: v = e * e; break;
         case MP_R_M: v = m; break;
@@ -405,19 +423,66 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
         case MP_R_AMZ: v = fabs(ez); break;
         case MP_R_EM: v = e * m; break;
         case MP_R_EMZ: v = e * ez; break;
-        case MP_R_MMZ: v = m * ez; break;
-        case MP_R_FMX: v = ex; break;
-        case MP_R_FMY: v = ey; break;
-        case MP_R_FMZ: v = ez; break;
-        case MP_R_FE: v = e; break;
-        default: break;
+        default: v = m * ez; break;  // MP_R_MMZ
       }
-      if (lane <= MP_R_MMZ) acc[lane] += static_cast<double>(v);
-      else if (lane <= MP_R_FE && s == nsweeps - 1) acc[lane] = static_cast<double>(v);
+      if (lane >= n) v = Real(0);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        if (o < R) v += A::shfl(v, o);
+      }
+      if (lane == 0) acc[k] += static_cast<double>(v);
     }
-    // red[] is rewritten only after the next colour-0 barrier, which warp 0
-    // reaches after reading it.
+  };
+  for (int64_t s = 0; s < nsweeps; ++s) {
+    const uint32_t sw = static_cast<uint32_t>(s);
+    Partials<Real> part{Real(0), Real(0), Real(0), Real(0)};
+    if (s < P.n_therm) {
+      half_sweep<Real, Geom, false, false>(geo, 0, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf, bp,
+                                    accepted, part);
+      group_sync(tp, bar);
+      half_sweep<Real, Geom, false, false>(geo, 1, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf, bp,
+                                    accepted, part);
+      group_sync(tp, bar);
+      continue;
+    }
+    // Measurement sweep j.  Colour-0 sites keep their values during the
+    // colour-1 pass, so the colour-1 local fields give every bond once.
+    const int64_t j = s - P.n_therm;
+    half_sweep<Real, Geom, true, false>(geo, 0, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf, bp,
+                                        accepted, part);
+    group_sync(tp, bar);
+    if (j > 0 && (j % R) == 0) flush(j - R, R);  // the previous half is complete
+    half_sweep<Real, Geom, true, true>(geo, 1, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf, bp,
+                                       accepted, part);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      part.eb += A::shfl(part.eb, o);
+      part.mx += A::shfl(part.mx, o);
+      part.my += A::shfl(part.my, o);
+      part.mz += A::shfl(part.mz, o);
+    }
+    if (lane == 0) {
+      Real* r = slot_ptr(j) + warp * kRedSlots;
+      r[0] = part.eb;
+      r[1] = part.mx;
+      r[2] = part.my;
+      r[3] = part.mz;
+    }
+    group_sync(tp, bar);
   }
+  {
+    const int64_t last = P.n_meas - 1;
+    flush(last - last % R, static_cast<int>(last % R) + 1);
+    if (tid == 0) {  // the final state: the paper's per-path output
+      Real e, ex, ey, ez;
+      observe(slot_ptr(last), e, ex, ey, ez);
+      acc[MP_R_FMX] = static_cast<double>(ex);
+      acc[MP_R_FMY] = static_cast<double>(ey);
+      acc[MP_R_FMZ] = static_cast<double>(ez);
+      acc[MP_R_FE] = static_cast<double>(e);
+    }
+  }
+  group_sync(tp, bar);
 
   // Final state: acceptance count and the worst | |S| - 1 |, reduced over the group.
   Real worst = Real(0);
@@ -428,22 +493,24 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
       worst = fmax(worst, fabs(sqrt(x * x + y * y + z * z) - Real(1)));
     }
   }
-  Real nacc = static_cast<Real>(accepted);
+  double nacc = static_cast<double>(accepted);
+  double wst = static_cast<double>(worst);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    nacc += A::shfl(nacc, o);
-    worst = fmax(worst, A::shfl(worst, o));
+    nacc += __shfl_xor_sync(0xffffffffu, nacc, o);
+    wst = fmax(wst, __shfl_xor_sync(0xffffffffu, wst, o));
   }
+  double* fin = reinterpret_cast<double*>(red);  // the red area holds 2 doubles per warp
   if (lane == 0) {
-    red[warp * kRedSlots + 0] = nacc;
-    red[warp * kRedSlots + 1] = worst;
+    fin[2 * warp + 0] = nacc;
+    fin[2 * warp + 1] = wst;
   }
   group_sync(tp, bar);
   if (tid == 0) {
     double tot = 0.0, wmax = 0.0;
     for (int w = 0; w < nwarps; ++w) {
-      tot += static_cast<double>(red[w * kRedSlots + 0]);
-      wmax = fmax(wmax, static_cast<double>(red[w * kRedSlots + 1]));
+      tot += fin[2 * w + 0];
+      wmax = fmax(wmax, fin[2 * w + 1]);
     }
     double* rec = P.records + (sy.rec_offset + path) * MP_NREC;
     const double inv = 1.0 / static_cast<double>(P.n_meas);
@@ -486,14 +553,20 @@ __device__ __forceinline__ void dispatch_path(const DevSystem& sy, int sys_idx, 
                                               const SweepParams& P, unsigned char* slice, int tid,
                                               int tp, int bar);
 
-// Largest CTA of each precision: the FP64 form needs more than 64 registers.
-template <typename Real>
+// Largest CTA of each kernel.  The FP64 form needs more than 64 registers;
+// FP32 lattices up to L = 16 run 512-thread CTAs with up to 128 registers per
+// thread, which buys the unrolled column walk its instruction-level
+// parallelism; larger lattices keep 1024-thread CTAs for occupancy.
+template <typename Real, int kLattice>
 struct CtaLimit {
-  static constexpr int value = sizeof(Real) == 8 ? 512 : kMaxCta;
+  static constexpr int value =
+      (sizeof(Real) == 8 || (kLattice > 0 && kLattice <= 16) || kLattice == kChainKernel) ? 512
+                                                                                           : kMaxCta;
 };
 
 template <typename Real, int kLattice>
-__global__ void __launch_bounds__(CtaLimit<Real>::value, 1) sweep_kernel(const SweepParams P) {
+__global__ void __launch_bounds__(CtaLimit<Real, kLattice>::value, 1)
+    sweep_kernel(const SweepParams P) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_item;
   for (;;) {

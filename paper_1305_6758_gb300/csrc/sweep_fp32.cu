@@ -50,8 +50,9 @@ static const void* kernel_of(int variant) {
 bool SUFFIX(sweep_supports_L)(int L) { return L > 0 && kernel_of(L) != nullptr; }
 
 // Raises a variant's dynamic shared-memory limit to what the device allows
-// beside the kernel's static shared memory; returns that limit in *max_dynamic.
-cudaError_t SUFFIX(sweep_prepare)(int variant, int device, int* max_dynamic) {
+// beside the kernel's static shared memory; returns that limit in
+// *max_dynamic and the kernel's largest CTA in *max_threads.
+cudaError_t SUFFIX(sweep_prepare)(int variant, int device, int* max_dynamic, int* max_threads) {
   const void* k = kernel_of(variant);
   if (!k) return cudaErrorInvalidValue;
   int optin = 0;
@@ -61,6 +62,7 @@ cudaError_t SUFFIX(sweep_prepare)(int variant, int device, int* max_dynamic) {
   e = cudaFuncGetAttributes(&fa, k);
   if (e != cudaSuccess) return e;
   *max_dynamic = optin - static_cast<int>(fa.sharedSizeBytes);
+  *max_threads = fa.maxThreadsPerBlock;
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, *max_dynamic);
 }
 
