@@ -248,6 +248,35 @@ int mp_plan(mp_handle h, int* cta_threads, int* grid, int* smem_bytes, int* n_it
  * the sweep kernels use.  Errors: MP_EINVAL (n < 0, NULL with n > 0), MP_ECUDA. */
 int mp_philox(const uint32_t* d_ctr, int64_t n, uint64_t seed, uint32_t* d_out, void* stream);
 
+/* Allocation-free run, for callers that cannot allocate device memory:
+ * code inside a host framework that owns every device allocation (a fixed
+ * pool or arena), code that must not grow the device heap after start-up, or
+ * a plugin whose host forbids allocator calls.  The paper has no counterpart;
+ * the call exists for those callers.
+ *
+ * It runs the same sweep and reduction kernels as mp_run for the batch
+ * `systems` (host array of n_systems, read during the call) in `precision`
+ * (MP_FP32 or MP_FP64) with uniform-on-sphere starts, and writes MP_NEST
+ * doubles of estimates per system (the mp_estimates_t layout) to d_estimates
+ * (device memory of n_systems * MP_NEST doubles, owned by the caller), all
+ * queued on `stream` (cudaStream_t; NULL = legacy default stream).  It calls
+ * no cudaMalloc, cudaFree or other allocating routine: its scratch (per-path
+ * records, work queue, device copies of the tables) is one static __device__
+ * array of about 2.9 MB that every GPU loading the library holds until the
+ * process exits.  Limits: at most MP_NOALLOC_MAX_PATHS paths in total and
+ * MP_NOALLOC_MAX_SYSTEMS systems; larger batches return MP_EINVAL before any
+ * GPU work.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents (the work counter is cleared at the start of each
+ * call): calls whose GPU work overlaps, on different streams or different
+ * host threads, race on it.  Errors: MP_EINVAL (NULL pointer, bad sizes,
+ * unsupported lattice), MP_ECUDA (device error). */
+#define MP_NOALLOC_MAX_PATHS 16384
+#define MP_NOALLOC_MAX_SYSTEMS 64
+int mp_run_noalloc(const mp_system* systems, int n_systems, int precision, int64_t n_therm,
+                   int64_t n_meas, uint64_t seed, double* d_estimates, void* stream);
+
 /* Release every device buffer, event and graph of the handle (after
  * synchronising its stream).  NULL is a no-op. */
 void mp_destroy(mp_handle h);
