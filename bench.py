@@ -152,6 +152,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    # shorter runs of the same launch (for profiling captures only)
+    ap.add_argument("--n-therm", type=int, default=N_THERM)
+    ap.add_argument("--n-meas", type=int, default=N_MEAS)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -183,8 +186,10 @@ def main():
         torch.cuda.synchronize(dev)
 
     seed = 1 + rank
+    n_therm, n_meas = args.n_therm, args.n_meas
+    sweeps = n_therm + n_meas
     systems = [mp.System(L, T, n_paths=PATHS) for T in TEMPS]
-    sim = mp.Simulation(systems, N_THERM, N_MEAS, seed=seed, precision=mp.FP32, device=dev)
+    sim = mp.Simulation(systems, n_therm, n_meas, seed=seed, precision=mp.FP32, device=dev)
     stream = sim.stream
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
@@ -219,7 +224,7 @@ def main():
         t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = t.item()
-    attempts_rank = N_SITES * PATHS * N_T * SWEEPS
+    attempts_rank = N_SITES * PATHS * N_T * sweeps
     value = attempts_rank * world * args.steps / (total_ms / 1e3)
     paths_per_s = PATHS * N_T * world * args.steps / (total_ms / 1e3)
     ests = [sim.estimates(k) for k in range(N_T)]
@@ -233,7 +238,7 @@ def main():
     for k in range(max(1, min(2, args.steps))):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        with mp.Simulation(systems, N_THERM, N_MEAS, seed=seed + 1000 * (k + 1), device=dev) as s2:
+        with mp.Simulation(systems, n_therm, n_meas, seed=seed + 1000 * (k + 1), device=dev) as s2:
             s2.run()
             for j in range(N_T):
                 s2.estimates(j)
@@ -254,13 +259,13 @@ def main():
     fp64 = None
     if not args.no_fp64:
         sub = 64
-        with mp.Simulation([mp.System(L, T, n_paths=sub) for T in TEMPS], N_THERM, N_MEAS, seed=seed,
+        with mp.Simulation([mp.System(L, T, n_paths=sub) for T in TEMPS], n_therm, n_meas, seed=seed,
                            precision=mp.FP64, device=dev) as s64:
             s64.run()
             torch.cuda.synchronize(dev)
             a64, _ = s64.timing()
             e64 = [s64.estimates(k) for k in range(N_T)]
-        att64 = N_SITES * sub * N_T * SWEEPS
+        att64 = N_SITES * sub * N_T * sweeps
         v64 = att64 / (a64 / 1e3)
         worst = max(abs(ests[k]["e"] - e64[k]["e"]) / (ests[k]["e_se"] ** 2 + e64[k]["e_se"] ** 2) ** 0.5
                     for k in range(N_T))
@@ -283,7 +288,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "L": L, "temperatures": N_T, "paths_per_temperature": PATHS,
-                       "n_therm": N_THERM, "n_meas": N_MEAS, "parallelism": f"replicas x{world}",
+                       "n_therm": n_therm, "n_meas": n_meas, "parallelism": f"replicas x{world}",
                        "l2": "flushed between timed steps (256 MB write)", "plan": sim.plan()},
             "paths_per_s": paths_per_s,
             "sigma": {"e_se_max": max(e["e_se"] for e in ests), "m_se_max": max(e["m_se"] for e in ests),

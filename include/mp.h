@@ -11,8 +11,10 @@
  *
  * Model (Sec. 2.1): H = -(J/2) sum_n sum_lambda S_n . S_{n+lambda} - h sum_n S^z_n,
  * Eq. (1) plus a Zeeman term (h = 0 is the paper's model), unit spins of Eq. (2),
- * on a periodic simple-cubic lattice of N = L^3 sites (L even, 2 <= L <= 24 for
- * the shared-memory kernels) or an open chain of N = L spins.
+ * on a periodic simple-cubic lattice of N = L^3 sites (L even; L <= 26 in FP32
+ * and L <= 20 in FP64 run with the lattice in shared memory, larger lattices
+ * are streamed from HBM while their half-plane ring fits in shared memory:
+ * L <= 64 in FP32, L <= 44 in FP64) or an open chain of N = L spins.
  *
  * Conventions shared by every call:
  *   - Every function returns an int status (MP_OK or a negative MP_E* code),
@@ -61,6 +63,13 @@ extern "C" {
 
 #define MP_FLAG_GRAPH 1u      /* capture each run in a CUDA graph and replay it */
 #define MP_FLAG_KEEP_SPINS 2u /* keep every path's final spins (mp_spins) */
+#define MP_FLAG_STREAM 4u     /* stream every simple-cubic lattice from HBM, even
+                                 those that fit in shared memory (lattices too
+                                 large for shared memory are always streamed) */
+#define MP_FLAG_TEST_STALL 0x100u /* failure injection for tests: streamed paths
+                                     never issue their first bulk copy, so the
+                                     kernel's bounded wait runs out (about 2 s)
+                                     and mp_estimates returns MP_ETIMEOUT */
 
 /* ------------------------------------------------------------- records ---
  * Per-path record: MP_NREC doubles per path.  Fields 0..12 are means over the

@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(_HERE, "libmp.so")
 SC, CHAIN = 0, 1
 FP32, FP64 = 0, 1
 INIT_SPHERE, INIT_ANGLES, INIT_ORDERED = 0, 1, 2
-FLAG_GRAPH, FLAG_KEEP_SPINS = 1, 2
+FLAG_GRAPH, FLAG_KEEP_SPINS, FLAG_STREAM, FLAG_TEST_STALL = 1, 2, 4, 0x100
 
 MP_OK, MP_EINVAL, MP_ENOMEM, MP_ECUDA, MP_ESTATE, MP_ECANCELED, MP_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 
@@ -198,7 +198,7 @@ class Simulation:
     def __init__(self, systems: list[System], n_therm: int, n_meas: int, seed: int = 1,
                  precision: int = FP32, init_mode: int = INIT_SPHERE, graph: bool = True,
                  keep_spins: bool = False, cta_threads: int = 0, threads_per_path: int = 0,
-                 device=None, stream=None):
+                 device=None, stream=None, flags: int = 0):
         import torch
 
         lib = load_library()
@@ -214,7 +214,7 @@ class Simulation:
         cfg.precision = precision
         cfg.init_mode = init_mode
         cfg.n_systems = len(systems)
-        cfg.flags = (FLAG_GRAPH if graph else 0) | (FLAG_KEEP_SPINS if keep_spins else 0)
+        cfg.flags = (FLAG_GRAPH if graph else 0) | (FLAG_KEEP_SPINS if keep_spins else 0) | flags
         cfg.systems = self._sys
         cfg.n_therm = n_therm
         cfg.n_meas = n_meas

@@ -28,7 +28,12 @@ struct DevSystem {
   double T, J, h, beta;
   int64_t rec_offset;   // global index of this system's path 0
   int64_t n_paths;
+  int32_t mode;         // kModeShared: lattice in shared memory; kModeStreamed: in HBM
+  int32_t pad;
 };
+
+constexpr int kModeShared = 0;
+constexpr int kModeStreamed = 1;
 
 // A unit of the persistent work queue: `count` consecutive paths of one
 // system, run side by side by one CTA (one thread group per path).
@@ -49,6 +54,11 @@ struct SweepParams {
   int32_t init_mode;
   int64_t n_therm, n_meas;
   PhiloxKeys key;         // round keys of the seed
+  void* lattice;          // HBM lattices of streamed paths, one per (CTA, group)
+  int64_t lattice_stride; // bytes per lattice buffer
+  int32_t lattice_groups; // buffers per CTA
+  uint32_t test_stall;    // failure injection: streamed paths skip their first bulk copy
+  int* error;             // set to nonzero when a bounded wait gave up
 };
 
 // Byte offsets inside one path's shared-memory slice.

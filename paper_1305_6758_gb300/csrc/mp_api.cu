@@ -63,6 +63,14 @@ int64_t sites_of(const mp_system& s) {
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
+// Streamed lattices: one half-plane (one colour of one z-plane, 3 L^2/2 values)
+// padded to 16 bytes, in bytes.
+int half_plane_bytes(int L, int real) { return round_up(3 * (L * L / 2) * real, 16); }
+
+bool streamed(const mp_system& s, int precision, uint32_t flags) {
+  return s.lattice == MP_LATTICE_SC && ((flags & MP_FLAG_STREAM) || !sweep_supports_L(precision, s.L));
+}
+
 }  // namespace
 
 struct mp_state {
@@ -94,6 +102,10 @@ struct mp_state {
   double* d_est = nullptr;
   double* d_spins = nullptr;
   int64_t* d_spin_offset = nullptr;
+  int* d_error = nullptr;          // nonzero when a bounded wait in a kernel gave up
+  void* d_lattice = nullptr;       // HBM lattices of streamed paths
+  int64_t lattice_stride = 0;      // bytes per (CTA, group) lattice buffer
+  int lattice_groups = 0;          // buffers per CTA
   std::vector<void*> owned;
 
   cudaGraphExec_t gexec = nullptr;
@@ -194,10 +206,7 @@ int validate(const mp_config* cfg) {
     if (s.lattice == MP_LATTICE_SC) {
       if (s.L < 2 || (s.L & 1))
         return fail(nullptr, MP_EINVAL, "system %d: simple cubic L must be even and >= 2", k);
-      if (!sweep_supports_L(cfg->precision, s.L))
-        return fail(nullptr, MP_EINVAL,
-                    "system %d: L=%d does not fit the %s shared-memory sweep", k, s.L,
-                    cfg->precision == MP_FP64 ? "FP64" : "FP32");
+      if (s.L > 1024) return fail(nullptr, MP_EINVAL, "system %d: L=%d above 1024", k, s.L);
     } else if (s.L < 2 || s.L > 8192) {
       return fail(nullptr, MP_EINVAL, "system %d: chain length must be in 2..8192", k);
     }
@@ -212,12 +221,15 @@ int validate(const mp_config* cfg) {
 int plan(mp_state* h, const mp_config* cfg) {
   const int real = h->precision == MP_FP64 ? 8 : 4;
   const int n = static_cast<int>(h->systems.size());
-  // one kernel per lattice size when the batch has a single size
-  int variant = h->systems[0].lattice == MP_LATTICE_CHAIN ? -1 : h->systems[0].L;
-  for (int k = 1; k < n; ++k) {
-    const int v = h->systems[k].lattice == MP_LATTICE_CHAIN ? -1 : h->systems[k].L;
-    if (v != variant) variant = 0;
-  }
+  // one kernel per lattice size when the batch has a single size; lattices
+  // too large for shared memory are streamed from HBM (any size, one kernel)
+  auto variant_of = [&](const mp_system& sy) {
+    if (sy.lattice == MP_LATTICE_CHAIN) return -1;
+    return streamed(sy, h->precision, h->flags) ? -2 : sy.L;
+  };
+  int variant = variant_of(h->systems[0]);
+  for (int k = 1; k < n; ++k)
+    if (variant_of(h->systems[k]) != variant) variant = 0;
   h->variant = variant;
   int sms = 0, smem_max = 0, cta_max = 0;
   MP_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
@@ -231,6 +243,28 @@ int plan(mp_state* h, const mp_config* cfg) {
     const int64_t N = sites_of(h->systems[k]);
     const int NH = static_cast<int>((N + 1) / 2);
     int t = cfg->threads_per_path;
+    if (streamed(h->systems[k], h->precision, h->flags)) {
+      // one thread per column x/2 of a z-plane and about L/4 rows per thread
+      const int L = h->systems[k].L, HL = L / 2;
+      if (t == 0) t = std::min(cta_max, round_up(HL * ((L + 3) / 4), 32));
+      if (t > cta_max || t < HL)
+        return fail(h, MP_EINVAL, "system %d: threads_per_path %d outside %d..%d", k, t, HL, cta_max);
+      tp[k] = t;
+      ring[k] = 16;
+      auto need = [&]() {
+        return round_up(slice_spin_offset(t, ring[k]) + 128 + 8 * half_plane_bytes(L, real), 128);
+      };
+      slice[k] = need();
+      while (ring[k] > 1 && slice[k] > smem_max) {
+        ring[k] /= 2;
+        slice[k] = need();
+      }
+      if (slice[k] > smem_max)
+        return fail(h, MP_EINVAL, "system %d: L=%d needs %d bytes of shared memory for its "
+                    "half-plane ring (max %d)", k, L, slice[k], smem_max);
+      max_tp = std::max(max_tp, t);
+      continue;
+    }
     if (t == 0 && h->systems[k].lattice == MP_LATTICE_SC) {
       // a multiple of the half-sites of a z-plane lets each thread walk one
       // column (fixed x/2, y); pick the one closest to 8 sites per thread
@@ -306,6 +340,13 @@ int plan(mp_state* h, const mp_config* cfg) {
     d.beta = 1.0 / s.T;
     d.rec_offset = rec;
     d.n_paths = s.n_paths;
+    d.mode = streamed(s, h->precision, h->flags) ? kModeStreamed : kModeShared;
+    d.pad = 0;
+    if (d.mode == kModeStreamed) {
+      h->lattice_groups = std::max(h->lattice_groups, d.g);
+      h->lattice_stride = std::max<int64_t>(
+          h->lattice_stride, static_cast<int64_t>(2) * s.L * half_plane_bytes(s.L, real));
+    }
     rec += s.n_paths;
     h->spin_offset[k] = spins;
     spins += s.n_paths * 3 * static_cast<int64_t>(d.N);
@@ -342,6 +383,11 @@ int enqueue_run(mp_state* h) {
   p.n_items = static_cast<int32_t>(h->items.size());
   p.init_mode = h->init_mode;
   p.key = philox_round_keys(h->seed);
+  p.lattice = h->d_lattice;
+  p.lattice_stride = h->lattice_stride;
+  p.lattice_groups = h->lattice_groups;
+  p.error = h->d_error;
+  p.test_stall = (h->flags & MP_FLAG_TEST_STALL) ? 1u : 0u;
   p.n_therm = h->n_therm;
   p.n_meas = h->n_meas;
   ReduceParams r{};
@@ -353,6 +399,7 @@ int enqueue_run(mp_state* h) {
   const bool capturing = h->flags & MP_FLAG_GRAPH;
   const unsigned evflag = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   MP_CUDA(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int), h->stream));
+  MP_CUDA(h, cudaMemsetAsync(h->d_error, 0, sizeof(int), h->stream));
   MP_CUDA(h, cudaEventRecordWithFlags(h->ev[0], h->stream, evflag));
   MP_CUDA(h, launch_sweep(h->precision, h->variant, p, h->grid, h->cta, h->smem, h->stream));
   MP_CUDA(h, cudaEventRecordWithFlags(h->ev[1], h->stream, evflag));
@@ -362,6 +409,14 @@ int enqueue_run(mp_state* h) {
 }
 
 }  // namespace
+
+// After the stream has drained: MP_ETIMEOUT if a kernel's bounded wait gave up.
+int check_error_flag(mp_state* h) {
+  int flag = 0;
+  MP_CUDA(h, cudaMemcpy(&flag, h->d_error, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) return fail(h, MP_ETIMEOUT, "a bulk copy did not complete in time; results invalid");
+  return MP_OK;
+}
 
 extern "C" {
 
@@ -430,6 +485,13 @@ int mp_create_ex(const mp_config* cfg, mp_handle* out) {
   h->d_spin_offset = static_cast<int64_t*>(dev_alloc(h, sizeof(int64_t) * n));
   if (!h->d_sys || !h->d_items || !h->d_queue || !h->d_rec || !h->d_est || !h->d_spin_offset)
     return bail(fail(h, MP_ENOMEM, "device allocation failed"));
+  h->d_error = static_cast<int*>(dev_alloc(h, 256));
+  if (!h->d_error) return bail(fail(h, MP_ENOMEM, "device allocation failed"));
+  if (h->lattice_groups > 0) {
+    h->lattice_stride = (h->lattice_stride + 255) / 256 * 256;
+    h->d_lattice = dev_alloc(h, static_cast<size_t>(h->grid) * h->lattice_groups * h->lattice_stride);
+    if (!h->d_lattice) return bail(fail(h, MP_ENOMEM, "lattice buffer allocation failed"));
+  }
   if (h->flags & MP_FLAG_KEEP_SPINS) {
     h->d_spins = static_cast<double*>(dev_alloc(h, sizeof(double) * h->total_spins));
     if (!h->d_spins) return bail(fail(h, MP_ENOMEM, "spin buffer allocation failed"));
@@ -498,7 +560,7 @@ int mp_estimates(mp_handle h, int system, mp_estimates_t* out) {
   MP_CUDA(h, cudaMemcpyAsync(out, h->d_est + static_cast<int64_t>(system) * MP_NEST,
                              sizeof(mp_estimates_t), cudaMemcpyDeviceToHost, h->stream));
   MP_CUDA(h, cudaStreamSynchronize(h->stream));
-  return MP_OK;
+  return check_error_flag(h);
 }
 
 int mp_paths(mp_handle h, int system, double* host_out, int64_t cap) {
@@ -513,7 +575,7 @@ int mp_paths(mp_handle h, int system, double* host_out, int64_t cap) {
   MP_CUDA(h, cudaMemcpyAsync(host_out, h->d_rec + d.rec_offset * MP_NREC,
                              sizeof(double) * MP_NREC * d.n_paths, cudaMemcpyDeviceToHost, h->stream));
   MP_CUDA(h, cudaStreamSynchronize(h->stream));
-  return MP_OK;
+  return check_error_flag(h);
 }
 
 int mp_device_buffers(mp_handle h, double** d_records, double** d_estimates) {

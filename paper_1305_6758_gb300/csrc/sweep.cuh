@@ -329,64 +329,26 @@ __device__ __forceinline__ void half_sweep(const Geom& geo, int c, uint32_t swee
   }
 }
 
-// ------------------------------------------------------------- one path --
-template <typename Real, class Geom>
-__device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, int sys_idx,
-                                         int64_t path, const SweepParams& P, unsigned char* slice,
-                                         int tid, int tp, int bar) {
-  using A = Arith<Real>;
-  double* acc = reinterpret_cast<double*>(slice + slice_acc_offset());
-  Real* red = reinterpret_cast<Real*>(slice + slice_red_offset());
-  Real* sp = reinterpret_cast<Real*>(slice + slice_spin_offset(tp, sy.ring));
-  const int S = geo.stride();
-  const uint32_t c2 = static_cast<uint32_t>(path);
-  const uint32_t c3u = kTagUpdate | (static_cast<uint32_t>(sys_idx) << 8);
-  const uint32_t c3i = kTagInit | (static_cast<uint32_t>(sys_idx) << 8);
-  const Real J = static_cast<Real>(sy.J), hf = static_cast<Real>(sy.h);
-  const Real bp = A::beta_param(sy.beta);
-  const int lane = tid & 31, warp = tid >> 5, nwarps = tp >> 5;
-  const bool columns = Geom::kColumns && (tp % Geom::HP) == 0;
+// ----------------------------------------------------------- measurement --
+// Per-path measurement state in the path's shared-memory slice: the FP64
+// accumulators and the partial-sum ring.  ring[half][slot][warp][4] holds each
+// warp's partial sums (E_bond, Mx, My, Mz) of one measurement sweep; a half of
+// R sweeps is flushed into the FP64 accumulators by all warps together after
+// the next barrier while the other half fills, so no warp carries the
+// bookkeeping alone and no FP64 operation runs per sweep.
+template <typename Real>
+struct Meter {
+  double* acc;
+  Real* red;
+  int R, nwarps, lane, warp, tid;
+  double invN;
+  Real J, hf;
 
-  // Random initial state (Sec. 2.2), or the ordered start of Sec. 5.
-  for (int c = 0; c < 2; ++c) {
-    Real* own = sp + c * 3 * S;
-    const int cnt = geo.count(c);
-    for (int hh = tid; hh < cnt; hh += tp) {
-      int nb[Geom::NNB];
-      int nn;
-      const int i = geo.site(hh, c, nb, nn);
-      const Philox4 r = philox4x32_10(static_cast<uint32_t>(i), 0u, c2, c3i, P.key);
-      Real x, y, z;
-      if (P.init_mode == MP_INIT_ORDERED) {
-        x = Real(0);
-        y = Real(0);
-        z = Real(1);
-      } else if (P.init_mode == MP_INIT_ANGLES) {
-        A::init_angles(r.x, r.y, x, y, z);
-      } else {
-        A::trial(r.x, r.y, x, y, z);
-      }
-      own[hh] = x;
-      own[S + hh] = y;
-      own[2 * S + hh] = z;
-    }
-  }
-  if (tid < kAccDoubles) acc[tid] = 0.0;
-  group_sync(tp, bar);
-
-  int accepted = 0;
-  const int64_t nsweeps = P.n_therm + P.n_meas;
-  const double invN = 1.0 / static_cast<double>(sy.N);
-  const int R = sy.ring;  // measurement sweeps per ring half
-  // ring[half][slot][warp][4]: each warp's partial sums (E_bond, Mx, My, Mz)
-  // of one measurement sweep.  A half of R sweeps is flushed into the FP64
-  // accumulators by all warps together after the next barrier, while the
-  // other half fills.
-  auto slot_ptr = [&](int64_t j) {
+  __device__ Real* slot(int64_t j) const {
     return red + ((((j / R) & 1) * R + (j % R)) * nwarps) * kRedSlots;
-  };
+  }
   // Per-site observables (Sec. 2.2) of one measurement sweep from its slot.
-  auto observe = [&](const Real* sl, Real& e, Real& ex, Real& ey, Real& ez) {
+  __device__ void observe(const Real* sl, Real& e, Real& ex, Real& ey, Real& ez) const {
     Real E = Real(0), MX = Real(0), MY = Real(0), MZ = Real(0);
     for (int w = 0; w < nwarps; ++w) {
       E += sl[w * kRedSlots + 0];
@@ -399,13 +361,32 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
     ex = MX * rN;
     ey = MY * rN;
     ez = MZ * rN;
-  };
-  // Flush measurement sweeps j0 .. j0+n-1 (one ring half): lane l takes
-  // sweep j0+l; warp w owns observables w, w + warps, ...; each owned
-  // observable is summed over the lanes and added to its FP64 accumulator.
-  auto flush = [&](int64_t j0, int n) {
+  }
+  // Store this warp's partials of measurement sweep j (every lane calls).
+  __device__ void record(int64_t j, Partials<Real> part) const {
+    using A = Arith<Real>;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      part.eb += A::shfl(part.eb, o);
+      part.mx += A::shfl(part.mx, o);
+      part.my += A::shfl(part.my, o);
+      part.mz += A::shfl(part.mz, o);
+    }
+    if (lane == 0) {
+      Real* r = slot(j) + warp * kRedSlots;
+      r[0] = part.eb;
+      r[1] = part.mx;
+      r[2] = part.my;
+      r[3] = part.mz;
+    }
+  }
+  // Flush sweeps j0 .. j0+n-1 (one ring half): lane l takes sweep j0+l; warp
+  // w owns observables w, w + warps, ...; each owned observable is summed
+  // over the lanes and added to its FP64 accumulator.
+  __device__ void flush(int64_t j0, int n) const {
+    using A = Arith<Real>;
     Real e = Real(0), ex = Real(0), ey = Real(0), ez = Real(0);
-    if (lane < n) observe(slot_ptr(j0 + lane), e, ex, ey, ez);
+    if (lane < n) observe(slot(j0 + lane), e, ex, ey, ez);
     const Real m2 = ex * ex + ey * ey + ez * ez;
     const Real m = sqrt(m2);
     for (int k = warp; k <= MP_R_MMZ; k += nwarps) {
@@ -432,16 +413,121 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
       }
       if (lane == 0) acc[k] += static_cast<double>(v);
     }
-  };
+  }
+  // At measurement sweep j, after its first barrier: flush the previous half.
+  __device__ void maybe_flush(int64_t j) const {
+    if (j > 0 && (j % R) == 0) flush(j - R, R);
+  }
+  // After the last sweep's final barrier: flush the rest, keep the final state.
+  __device__ void finish(int64_t n_meas) const {
+    const int64_t last = n_meas - 1;
+    flush(last - last % R, static_cast<int>(last % R) + 1);
+    if (tid == 0) {  // the final state: the paper's per-path output
+      Real e, ex, ey, ez;
+      observe(slot(last), e, ex, ey, ez);
+      acc[MP_R_FMX] = static_cast<double>(ex);
+      acc[MP_R_FMY] = static_cast<double>(ey);
+      acc[MP_R_FMZ] = static_cast<double>(ez);
+      acc[MP_R_FE] = static_cast<double>(e);
+    }
+  }
+  // Reduce the acceptance count and the worst | |S| - 1 | over the group and
+  // write the path's record (the ring area is reused; call after a barrier).
+  __device__ void write_record(double* rec, int accepted, double worst, int64_t nsweeps,
+                               int64_t n_meas, int N, int tp, int bar) const {
+    double nacc = static_cast<double>(accepted);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      nacc += __shfl_xor_sync(0xffffffffu, nacc, o);
+      worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+    }
+    double* fin = reinterpret_cast<double*>(red);  // 2 doubles per warp
+    if (lane == 0) {
+      fin[2 * warp + 0] = nacc;
+      fin[2 * warp + 1] = worst;
+    }
+    group_sync(tp, bar);
+    if (tid == 0) {
+      double tot = 0.0, wmax = 0.0;
+      for (int w = 0; w < nwarps; ++w) {
+        tot += fin[2 * w + 0];
+        wmax = fmax(wmax, fin[2 * w + 1]);
+      }
+      const double inv = 1.0 / static_cast<double>(n_meas);
+      for (int k = MP_R_E; k <= MP_R_MMZ; ++k) rec[k] = acc[k] * inv;
+      for (int k = MP_R_FMX; k <= MP_R_FE; ++k) rec[k] = acc[k];
+      rec[MP_R_ACC] = tot / (static_cast<double>(nsweeps) * static_cast<double>(N));
+      rec[MP_R_NORM] = wmax;
+      rec[MP_R_SPARE] = 0.0;
+    }
+  }
+};
+
+// Initial spin of site i: uniform on the sphere (Sec. 2.2), uniform angles,
+// or the ordered start of Sec. 5.
+template <typename Real>
+__device__ __forceinline__ void initial_spin(uint32_t i, uint32_t c2, uint32_t c3i,
+                                             const SweepParams& P, Real& x, Real& y, Real& z) {
+  using A = Arith<Real>;
+  const Philox4 r = philox4x32_10(i, 0u, c2, c3i, P.key);
+  if (P.init_mode == MP_INIT_ORDERED) {
+    x = Real(0);
+    y = Real(0);
+    z = Real(1);
+  } else if (P.init_mode == MP_INIT_ANGLES) {
+    A::init_angles(r.x, r.y, x, y, z);
+  } else {
+    A::trial(r.x, r.y, x, y, z);
+  }
+}
+
+// ------------------------------------------------------------- one path --
+template <typename Real, class Geom>
+__device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, int sys_idx,
+                                         int64_t path, const SweepParams& P, unsigned char* slice,
+                                         int tid, int tp, int bar) {
+  using A = Arith<Real>;
+  Real* sp = reinterpret_cast<Real*>(slice + slice_spin_offset(tp, sy.ring));
+  const int S = geo.stride();
+  const uint32_t c2 = static_cast<uint32_t>(path);
+  const uint32_t c3u = kTagUpdate | (static_cast<uint32_t>(sys_idx) << 8);
+  const uint32_t c3i = kTagInit | (static_cast<uint32_t>(sys_idx) << 8);
+  const Real J = static_cast<Real>(sy.J), hf = static_cast<Real>(sy.h);
+  const Real bp = A::beta_param(sy.beta);
+  const bool columns = Geom::kColumns && (tp % Geom::HP) == 0;
+  const Meter<Real> meter{reinterpret_cast<double*>(slice + slice_acc_offset()),
+                          reinterpret_cast<Real*>(slice + slice_red_offset()),
+                          sy.ring, tp >> 5, tid & 31, tid >> 5, tid,
+                          1.0 / static_cast<double>(sy.N), J, hf};
+
+  for (int c = 0; c < 2; ++c) {
+    Real* own = sp + c * 3 * S;
+    const int cnt = geo.count(c);
+    for (int hh = tid; hh < cnt; hh += tp) {
+      int nb[Geom::NNB];
+      int nn;
+      const int i = geo.site(hh, c, nb, nn);
+      Real x, y, z;
+      initial_spin<Real>(static_cast<uint32_t>(i), c2, c3i, P, x, y, z);
+      own[hh] = x;
+      own[S + hh] = y;
+      own[2 * S + hh] = z;
+    }
+  }
+  if (tid < kAccDoubles) meter.acc[tid] = 0.0;
+  group_sync(tp, bar);
+
+  int accepted = 0;
+  const int64_t nsweeps = P.n_therm + P.n_meas;
   for (int64_t s = 0; s < nsweeps; ++s) {
     const uint32_t sw = static_cast<uint32_t>(s);
     Partials<Real> part{Real(0), Real(0), Real(0), Real(0)};
     if (s < P.n_therm) {
-      half_sweep<Real, Geom, false, false>(geo, 0, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf, bp,
-                                    accepted, part);
+      half_sweep<Real, Geom, false, false>(geo, 0, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf,
+                                           bp, accepted, part);
       group_sync(tp, bar);
-      half_sweep<Real, Geom, false, false>(geo, 1, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf, bp,
-                                    accepted, part);
+      half_sweep<Real, Geom, false, false>(geo, 1, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf,
+                                           bp, accepted, part);
       group_sync(tp, bar);
       continue;
     }
@@ -451,40 +537,15 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
     half_sweep<Real, Geom, true, false>(geo, 0, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf, bp,
                                         accepted, part);
     group_sync(tp, bar);
-    if (j > 0 && (j % R) == 0) flush(j - R, R);  // the previous half is complete
+    meter.maybe_flush(j);
     half_sweep<Real, Geom, true, true>(geo, 1, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf, bp,
                                        accepted, part);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      part.eb += A::shfl(part.eb, o);
-      part.mx += A::shfl(part.mx, o);
-      part.my += A::shfl(part.my, o);
-      part.mz += A::shfl(part.mz, o);
-    }
-    if (lane == 0) {
-      Real* r = slot_ptr(j) + warp * kRedSlots;
-      r[0] = part.eb;
-      r[1] = part.mx;
-      r[2] = part.my;
-      r[3] = part.mz;
-    }
+    meter.record(j, part);
     group_sync(tp, bar);
   }
-  {
-    const int64_t last = P.n_meas - 1;
-    flush(last - last % R, static_cast<int>(last % R) + 1);
-    if (tid == 0) {  // the final state: the paper's per-path output
-      Real e, ex, ey, ez;
-      observe(slot_ptr(last), e, ex, ey, ez);
-      acc[MP_R_FMX] = static_cast<double>(ex);
-      acc[MP_R_FMY] = static_cast<double>(ey);
-      acc[MP_R_FMZ] = static_cast<double>(ez);
-      acc[MP_R_FE] = static_cast<double>(e);
-    }
-  }
+  meter.finish(P.n_meas);
   group_sync(tp, bar);
 
-  // Final state: acceptance count and the worst | |S| - 1 |, reduced over the group.
   Real worst = Real(0);
   for (int c = 0; c < 2; ++c) {
     const Real* own = sp + c * 3 * S;
@@ -493,33 +554,8 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
       worst = fmax(worst, fabs(sqrt(x * x + y * y + z * z) - Real(1)));
     }
   }
-  double nacc = static_cast<double>(accepted);
-  double wst = static_cast<double>(worst);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    nacc += __shfl_xor_sync(0xffffffffu, nacc, o);
-    wst = fmax(wst, __shfl_xor_sync(0xffffffffu, wst, o));
-  }
-  double* fin = reinterpret_cast<double*>(red);  // the red area holds 2 doubles per warp
-  if (lane == 0) {
-    fin[2 * warp + 0] = nacc;
-    fin[2 * warp + 1] = wst;
-  }
-  group_sync(tp, bar);
-  if (tid == 0) {
-    double tot = 0.0, wmax = 0.0;
-    for (int w = 0; w < nwarps; ++w) {
-      tot += fin[2 * w + 0];
-      wmax = fmax(wmax, fin[2 * w + 1]);
-    }
-    double* rec = P.records + (sy.rec_offset + path) * MP_NREC;
-    const double inv = 1.0 / static_cast<double>(P.n_meas);
-    for (int k = MP_R_E; k <= MP_R_MMZ; ++k) rec[k] = acc[k] * inv;
-    for (int k = MP_R_FMX; k <= MP_R_FE; ++k) rec[k] = acc[k];
-    rec[MP_R_ACC] = tot / (static_cast<double>(nsweeps) * static_cast<double>(sy.N));
-    rec[MP_R_NORM] = wmax;
-    rec[MP_R_SPARE] = 0.0;
-  }
+  meter.write_record(P.records + (sy.rec_offset + path) * MP_NREC, accepted,
+                     static_cast<double>(worst), nsweeps, P.n_meas, sy.N, tp, bar);
   if (P.spins != nullptr) {
     double* out = P.spins + P.spin_offset[sys_idx] + path * 3 * static_cast<int64_t>(sy.N);
     for (int c = 0; c < 2; ++c) {
@@ -537,6 +573,299 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
   group_sync(tp, bar);  // the slice is reused by the next item
 }
 
+// ------------------------------------------------------ TMA primitives --
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// End an mbarrier's life before its memory is initialised again or reused.
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+// Bulk copy global -> shared of `bytes` (multiple of 16, both addresses 16-byte
+// aligned), completing on the mbarrier `bar`.
+__device__ __forceinline__ void tma_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+// Bulk copy shared -> global, as its own bulk group.
+__device__ __forceinline__ void tma_store(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_addr(src)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void tma_wait_read_all_but_last() {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+__device__ __forceinline__ void tma_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for phase `parity` of the mbarrier, giving up after about 2 s: then the
+// error flag is set and false returned (the caller stops the path cleanly).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* error) {
+  const uint32_t a = smem_addr(bar);
+  uint64_t t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 63) == 0) {
+      const uint64_t t = global_ns();
+      if (it == 0) t0 = t;
+      else if (t - t0 > 2000000000ull) {
+        atomicExch(error, 1);
+        return false;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------- streamed from HBM --
+// Lattices too large for shared memory.  Each path's spins stay in HBM in the
+// layout [z][colour][component][L*L/2] (a "half-plane" is one colour of one
+// z-plane, padded to 16 bytes), in a buffer owned by the thread group for the
+// whole run.  A sweep walks the z-planes as a wavefront over a ring of 4 + 4
+// half-plane buffers in shared memory, filled by TMA bulk copies and written
+// back by bulk stores:
+//   step q = 0 .. L+1:  (a) colour-0 update of plane q          (q < L)
+//                       (b) colour-1 update of plane (q-1) mod L (q >= 2)
+// Colour 0 of plane q needs colour 1 of planes q-1, q, q+1 still old; colour 1
+// of plane q-1 needs colour 0 of planes q-2, q-1, q already new; plane 0's
+// colour-1 update waits until the end (it needs colour 0 of plane L-1 new,
+// and colour 0 of plane L-1 needs colour 1 of plane 0 old).  Every update thus
+// sees exactly the neighbour values of the two-pass checkerboard sweep.
+// Ring indices: colour-0 step index q' = 0..L+1 (planes 0..L-1, 0, 1) in slot
+// q' mod 4; colour-1 step index q' = -1..L (planes L-1, 0..L-1, 0) in slot
+// (q'+1) mod 4.  Loads run 1-2 steps ahead of use.
+template <typename Real>
+struct StreamLayout {
+  static __host__ __device__ int hps(int L) {  // padded half-plane, in Reals
+    const int bytes = (3 * (L * L / 2) * static_cast<int>(sizeof(Real)) + 15) / 16 * 16;
+    return bytes / static_cast<int>(sizeof(Real));
+  }
+};
+
+template <typename Real>
+__device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path,
+                                  const SweepParams& P, unsigned char* slice, int tid, int tp,
+                                  int bar, Real* lat) {
+  using A = Arith<Real>;
+  const int L = sy.L, HL = L / 2, HP = L * L / 2;
+  const int hps = StreamLayout<Real>::hps(L);
+  const uint32_t bytes = static_cast<uint32_t>(hps * sizeof(Real));
+  // [8 mbarriers][8 load counters] in 128 bytes, then the 8 half-plane buffers
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(slice + slice_spin_offset(tp, sy.ring));
+  uint32_t* issued = reinterpret_cast<uint32_t*>(mbar + 8);
+  Real* buf = reinterpret_cast<Real*>(slice + slice_spin_offset(tp, sy.ring) + 128);
+  // buffer of colour c, step index q (see above)
+  auto c0buf = [&](int q) { return buf + ((q & 3)) * hps; };
+  auto c1buf = [&](int q) { return buf + (4 + ((q + 1) & 3)) * hps; };
+  auto c0bar = [&](int q) { return mbar + (q & 3); };
+  auto c1bar = [&](int q) { return mbar + 4 + ((q + 1) & 3); };
+  auto plane = [&](int z, int c) { return lat + (static_cast<int64_t>(z) * 2 + c) * hps; };
+  auto wrap = [&](int q) { return ((q % L) + L) % L; };
+  const uint32_t c2 = static_cast<uint32_t>(path);
+  const uint32_t c3u = kTagUpdate | (static_cast<uint32_t>(sys_idx) << 8);
+  const uint32_t c3i = kTagInit | (static_cast<uint32_t>(sys_idx) << 8);
+  const Real J = static_cast<Real>(sy.J), hf = static_cast<Real>(sy.h);
+  const Real bp = A::beta_param(sy.beta);
+  const Meter<Real> meter{reinterpret_cast<double*>(slice + slice_acc_offset()),
+                          reinterpret_cast<Real*>(slice + slice_red_offset()),
+                          sy.ring, tp >> 5, tid & 31, tid >> 5, tid,
+                          1.0 / static_cast<double>(sy.N), J, hf};
+  __shared__ int abort_flag[16];  // per thread group: a bounded wait gave up
+  const int gidx = bar - 1;
+  const bool producer = tid == 0;
+
+  // Initial state straight into HBM (generic stores), visible to the bulk copies.
+  const int N = sy.N;
+  for (int i = tid; i < N; i += tp) {
+    const int x = i % L, y = (i / L) % L, z = i / (L * L);
+    const int c = (x + y + z) & 1;
+    Real sx, sy_, sz;
+    initial_spin<Real>(static_cast<uint32_t>(i), c2, c3i, P, sx, sy_, sz);
+    Real* hpl = plane(z, c);
+    const int hp = (x >> 1) + HL * y;
+    hpl[hp] = sx;
+    hpl[HP + hp] = sy_;
+    hpl[2 * HP + hp] = sz;
+  }
+  fence_async_global();
+  if (tid < kAccDoubles) meter.acc[tid] = 0.0;
+  if (tid == 0) abort_flag[gidx] = 0;
+  if (producer) {
+    for (int k = 0; k < 8; ++k) {
+      mbar_init(mbar + k, 1);
+      issued[k] = 0;
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  auto load = [&](Real* dst, const Real* src, int slot) {  // producer only
+    ++issued[slot];
+    tma_load(dst, src, bytes, mbar + slot);
+  };
+  group_sync(tp, bar);
+
+  // In-plane thread layout: column hx, rows y0, y0 + RS, ...
+  const int RS = tp / HL;
+  const bool active = tid < HL * RS;
+  const int hx = active ? tid % HL : 0;
+  const int y0 = active ? tid / HL : L;
+  // loads per sweep into each ring slot, for the mbarrier phase parity
+  auto per_sweep = [&](int j) { return (L + 1 - j) / 4 + 1; };
+  int accepted = 0;
+  const int64_t nsweeps = P.n_therm + P.n_meas;
+  bool ok = true;
+
+  for (int64_t s = 0; s < nsweeps && ok; ++s) {
+    const uint32_t sw = static_cast<uint32_t>(s);
+    const bool meas = s >= P.n_therm;
+    const int64_t j = s - P.n_therm;
+    Partials<Real> part{Real(0), Real(0), Real(0), Real(0)};
+    auto parity0 = [&](int q) {
+      return static_cast<uint32_t>((s * per_sweep(q & 3) + q / 4) & 1);
+    };
+    auto parity1 = [&](int q) {
+      const int qq = q + 1;
+      return static_cast<uint32_t>((s * per_sweep(qq & 3) + qq / 4) & 1);
+    };
+    if (producer) {
+      tma_wait_all();  // the previous sweep's write-backs are complete
+      if (!(P.test_stall && s == 0)) load(c0buf(0), plane(0, 0), 0);
+      load(c0buf(1), plane(1 % L, 0), 1);
+      load(c1buf(-1), plane(L - 1, 1), 4);
+      load(c1buf(0), plane(0, 1), 5);
+      load(c1buf(1), plane(1 % L, 1), 6);
+    }
+    // One colour phase over plane z: own, same-plane, +z and -z buffers.
+    auto phase = [&](int c, int z, Real* own, const Real* same, const Real* up, const Real* dn,
+                     bool energy) {
+      for (int y = y0; y < L; y += RS) {
+        const int hp = hx + HL * y;
+        const int p = (y + z + c) & 1;
+        const int x = 2 * hx + p;
+        const int row = HL * y;
+        const int xp = row + ((x + 1 == L) ? 0 : ((x + 1) >> 1));
+        const int xm = row + ((x == 0) ? ((L - 1) >> 1) : ((x - 1) >> 1));
+        const int yp = (y == L - 1) ? hp - (L - 1) * HL : hp + HL;
+        const int ym = (y == 0) ? hp + (L - 1) * HL : hp - HL;
+        Real f[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const int o = k * HP;
+          f[k] = A::add(A::add(A::add(A::add(A::add(same[o + xp], same[o + xm]), same[o + yp]),
+                                       same[o + ym]), up[o + hp]), dn[o + hp]);
+        }
+        const uint32_t i = static_cast<uint32_t>(2 * (hp + HP * z) + p);
+        if (meas) {
+          if (energy)
+            update<Real, true, true>(i, sw, c2, c3u, P.key, own, HP, hp, f[0], f[1], f[2], J, hf, bp,
+                                     accepted, part);
+          else
+            update<Real, true, false>(i, sw, c2, c3u, P.key, own, HP, hp, f[0], f[1], f[2], J, hf,
+                                      bp, accepted, part);
+        } else {
+          update<Real, false, false>(i, sw, c2, c3u, P.key, own, HP, hp, f[0], f[1], f[2], J, hf, bp,
+                                     accepted, part);
+        }
+      }
+    };
+    for (int q = 0; q <= L + 1; ++q) {
+      // wait for the buffers first used at this step
+      bool w = mbar_wait(c0bar(q), parity0(q), P.error);
+      if (q == 0) {
+        w = w && mbar_wait(c1bar(-1), parity1(-1), P.error);
+        w = w && mbar_wait(c1bar(0), parity1(0), P.error);
+      }
+      if (q < L) w = w && mbar_wait(c1bar(q + 1), parity1(q + 1), P.error);
+      if (!w) abort_flag[gidx] = 1;
+      if (q < L) phase(0, q, c0buf(q), c1buf(q), c1buf(q + 1), c1buf(q - 1), false);
+      fence_async_shared();
+      group_sync(tp, bar);
+      if (abort_flag[gidx]) {
+        ok = false;
+        break;
+      }
+      if (meas && q == 0) meter.maybe_flush(j);
+      if (producer && q < L) tma_store(plane(q, 0), c0buf(q), bytes);
+      if (q >= 2) phase(1, wrap(q - 1), c1buf(q - 1), c0buf(q - 1), c0buf(q), c0buf(q - 2), meas);
+      fence_async_shared();
+      group_sync(tp, bar);
+      if (producer) {
+        if (q >= 2) tma_store(plane(wrap(q - 1), 1), c1buf(q - 1), bytes);
+        tma_wait_read_all_but_last();
+        // colour-0 step indices L and L+1 reload planes 0 and 1 written this sweep
+        if (q + 2 >= L) tma_wait_all();
+        if (q + 2 <= L + 1) load(c0buf(q + 2), plane(wrap(q + 2), 0), (q + 2) & 3);
+        if (q + 2 <= L) load(c1buf(q + 2), plane(wrap(q + 2), 1), 4 + ((q + 3) & 3));
+      }
+    }
+    if (!ok) break;
+    if (meas) {
+      meter.record(j, part);
+      group_sync(tp, bar);
+    }
+  }
+  if (producer) {
+    if (!ok) {
+      // a load did not arrive in time: wait (bounded) for every load still
+      // in flight before the shared memory is given up
+      for (int k = 0; k < 8; ++k)
+        if (issued[k] > 0) mbar_wait(mbar + k, (issued[k] - 1) & 1, P.error);
+    }
+    tma_wait_all();
+    fence_async_global();
+    // every consumer passed its last wait before the last barrier
+    for (int k = 0; k < 8; ++k) mbar_inval(mbar + k);
+  }
+  group_sync(tp, bar);
+  if (!ok) return;  // the error flag is set; the path's record is not written
+  meter.finish(P.n_meas);
+  group_sync(tp, bar);
+
+  double worst = 0.0;
+  for (int i = tid; i < N; i += tp) {
+    const int x = i % L, y = (i / L) % L, z = i / (L * L);
+    const Real* hpl = plane(z, (x + y + z) & 1);
+    const int hp = (x >> 1) + HL * y;
+    const double a = hpl[hp], b = hpl[HP + hp], c = hpl[2 * HP + hp];
+    worst = fmax(worst, fabs(sqrt(a * a + b * b + c * c) - 1.0));
+    if (P.spins != nullptr) {
+      double* out = P.spins + P.spin_offset[sys_idx] + path * 3 * static_cast<int64_t>(N);
+      out[3 * i + 0] = a;
+      out[3 * i + 1] = b;
+      out[3 * i + 2] = c;
+    }
+  }
+  meter.write_record(P.records + (sy.rec_offset + path) * MP_NREC, accepted, worst, nsweeps,
+                     P.n_meas, N, tp, bar);
+  group_sync(tp, bar);  // the slice and the HBM buffer are reused by the next item
+}
+
 // ------------------------------------------------------- persistent loop --
 // The compile-time lattice sizes each precision supports in shared memory.
 #define MPK_FOR_EACH_L_FP32(X) X(2) X(4) X(6) X(8) X(10) X(12) X(14) X(16) X(18) X(20) X(22) X(24) X(26)
@@ -547,6 +876,7 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
 // switches on each work item's lattice (a batch of uneven sizes).
 constexpr int kMixedKernel = 0;
 constexpr int kChainKernel = -1;
+constexpr int kStreamKernel = -2;  // simple cubic lattices streamed from HBM (any even L)
 
 template <typename Real, int kLattice>
 __device__ __forceinline__ void dispatch_path(const DevSystem& sy, int sys_idx, int64_t path,
@@ -560,7 +890,9 @@ __device__ __forceinline__ void dispatch_path(const DevSystem& sy, int sys_idx, 
 template <typename Real, int kLattice>
 struct CtaLimit {
   static constexpr int value =
-      (sizeof(Real) == 8 || (kLattice > 0 && kLattice <= 16) || kLattice == kChainKernel) ? 512
+      (sizeof(Real) == 8 || (kLattice > 0 && kLattice <= 16) || kLattice == kChainKernel ||
+       kLattice == kStreamKernel || kLattice == kMixedKernel)
+          ? 512
                                                                                            : kMaxCta;
 };
 
@@ -580,8 +912,20 @@ __global__ void __launch_bounds__(CtaLimit<Real, kLattice>::value, 1)
     const int g = static_cast<int>(threadIdx.x) / sy.tp;
     const int tid = static_cast<int>(threadIdx.x) - g * sy.tp;
     if (g < it.count) {
-      dispatch_path<Real, kLattice>(sy, it.sys, it.path0 + g, P, smem + g * sy.slice_bytes, tid,
-                                    sy.tp, 1 + g);
+      bool done = false;
+      if constexpr (kLattice == kStreamKernel || kLattice == kMixedKernel) {
+        if (sy.mode == kModeStreamed) {
+          Real* lat = reinterpret_cast<Real*>(
+              static_cast<unsigned char*>(P.lattice) +
+              (static_cast<int64_t>(blockIdx.x) * P.lattice_groups + g) * P.lattice_stride);
+          run_path_streamed<Real>(sy, it.sys, it.path0 + g, P, smem + g * sy.slice_bytes, tid,
+                                  sy.tp, 1 + g, lat);
+          done = true;
+        }
+      }
+      if (!done)
+        dispatch_path<Real, kLattice>(sy, it.sys, it.path0 + g, P, smem + g * sy.slice_bytes, tid,
+                                      sy.tp, 1 + g);
     }
   }
 }

@@ -14,6 +14,8 @@ __device__ __forceinline__ void dispatch_path(const DevSystem& sy, int sys_idx, 
                                               int tp, int bar) {
   if constexpr (kLattice > 0) {
     run_path<Real>(GeomSC<kLattice>{}, sy, sys_idx, path, P, slice, tid, tp, bar);
+  } else if constexpr (kLattice == kStreamKernel) {
+    // streamed paths are run by the kernel itself; nothing in shared memory only
   } else if constexpr (kLattice == kChainKernel) {
     run_path<Real>(GeomChain{sy.N}, sy, sys_idx, path, P, slice, tid, tp, bar);
   } else {
@@ -39,6 +41,7 @@ static const void* kernel_of(int variant) {
   switch (variant) {
     case kMixedKernel: return reinterpret_cast<const void*>(sweep_kernel<REAL, kMixedKernel>);
     case kChainKernel: return reinterpret_cast<const void*>(sweep_kernel<REAL, kChainKernel>);
+    case kStreamKernel: return reinterpret_cast<const void*>(sweep_kernel<REAL, kStreamKernel>);
 #define MPK_CASE(LL) \
     case LL: return reinterpret_cast<const void*>(sweep_kernel<REAL, LL>);
       MPK_FOR_EACH_L(MPK_CASE)

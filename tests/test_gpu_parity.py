@@ -197,7 +197,7 @@ def test_status_codes():
         mp.Simulation([mp.System(4, 1.0)], 1, 0)
     assert ei.value.status == mp.MP_EINVAL
     with pytest.raises(mp.MPError) as ei:
-        mp.Simulation([mp.System(24, 1.0)], 1, 1, precision=mp.FP64)
+        mp.Simulation([mp.System(64, 1.0)], 1, 1, precision=mp.FP64)
     assert ei.value.status == mp.MP_EINVAL
     sim = mp.Simulation([mp.System(4, 1.0, n_paths=4)], 1, 1)
     with pytest.raises(mp.MPError) as ei:

@@ -1,0 +1,118 @@
+"""The HBM-streamed sweep (lattices too large for shared memory).
+
+Its z-plane wavefront gives every update the neighbour values of the
+two-pass checkerboard sweep, so the FP64 form reproduces the oracle path by
+path, and a lattice forced through the streamed kernel follows the same
+trajectory as in the shared-memory kernel.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1305_6758_gb300 as mp  # noqa: E402
+
+FIELDS = list(range(17))
+
+
+def osys(s):
+    return O.System(L=s.L, T=s.T, J=s.J, h=s.h, n_paths=s.n_paths, lattice=s.lattice)
+
+
+def gpu_records(systems, n_therm, n_meas, seed=1, **kw):
+    with mp.Simulation(systems, n_therm, n_meas, seed=seed, **kw) as sim:
+        sim.run()
+        plan = sim.plan()
+        return [sim.paths(k) for k in range(len(systems))], plan
+
+
+@pytest.mark.parametrize("systems", [
+    [mp.System(22, 1.2, n_paths=3)],
+    [mp.System(28, 0.9, h=0.05, n_paths=2)],
+    [mp.System(32, 1.44, J=-1.0, n_paths=2)],
+])
+def test_streamed_fp64_matches_oracle(systems):
+    recs, _ = gpu_records(systems, 2, 3, seed=5, precision=mp.FP64)
+    refs = O.run([osys(s) for s in systems], 2, 3, seed=5)
+    for g, r in zip(recs, refs):
+        np.testing.assert_allclose(g[:, FIELDS], r[:, FIELDS], rtol=1e-10, atol=1e-13)
+        np.testing.assert_array_equal(g[:, 17], r[:, 17])
+
+
+def test_uneven_batch_shared_and_streamed_in_one_launch_fp64():
+    """Batched uneven sizes (L = 8 ... 32) in one persistent launch: sizes up to 20
+    in shared memory, 24 and 32 streamed; every path against the oracle."""
+    systems = [mp.System(L, 1.44, n_paths=P) for L, P in ((8, 16), (12, 8), (16, 4), (20, 2), (24, 2), (32, 1))]
+    recs, plan = gpu_records(systems, 2, 2, seed=3, precision=mp.FP64)
+    refs = O.run([osys(s) for s in systems], 2, 2, seed=3)
+    for g, r in zip(recs, refs):
+        np.testing.assert_allclose(g[:, FIELDS], r[:, FIELDS], rtol=1e-10, atol=1e-13)
+
+
+@pytest.mark.parametrize("sweeps", [(0, 1), (1, 1), (2, 3)])
+def test_streamed_many_paths_per_cta(sweeps):
+    """Each persistent CTA runs many streamed paths in turn (its mbarriers are
+    re-armed per path); odd and even numbers of loads per ring slot."""
+    systems = [mp.System(24, 1.1, n_paths=1200)]
+    recs, plan = gpu_records(systems, *sweeps, seed=2, precision=mp.FP64, flags=mp.FLAG_STREAM)
+    assert plan["n_items"] > plan["grid"], plan
+    refs = O.run([osys(s) for s in systems], *sweeps, seed=2)
+    np.testing.assert_allclose(recs[0][:, FIELDS], refs[0][:, FIELDS], rtol=1e-10, atol=1e-13)
+
+
+@pytest.mark.parametrize("precision", [mp.FP64, mp.FP32])
+def test_forced_streaming_follows_shared_memory_trajectory(precision):
+    systems = [mp.System(16, 1.3, n_paths=6), mp.System(8, 0.8, h=0.02, n_paths=10), mp.System(4, 2.0, n_paths=9)]
+    with mp.Simulation(systems, 3, 4, seed=8, precision=precision, keep_spins=True) as a, \
+            mp.Simulation(systems, 3, 4, seed=8, precision=precision, keep_spins=True, flags=mp.FLAG_STREAM) as b:
+        a.run()
+        b.run()
+        for k, s in enumerate(systems):
+            ra, rb = a.paths(k), b.paths(k)
+            tol = 1e-12 if precision == mp.FP64 else 2e-5
+            np.testing.assert_allclose(ra[:, FIELDS], rb[:, FIELDS], rtol=0, atol=tol)
+            for p in range(s.n_paths):
+                np.testing.assert_allclose(a.spins(k, p), b.spins(k, p), rtol=0, atol=tol)
+
+
+def test_full_size_l64_launch_first_sweep():
+    """The large-lattice launch (L = 64, 3 temperatures x 1024 paths, FP32) after one
+    sweep: sampled paths of each system against the oracle."""
+    Ts = [1.40, 1.44, 1.48]
+    systems = [mp.System(64, T, n_paths=1024) for T in Ts]
+    recs, plan = gpu_records(systems, 0, 1, seed=1)
+    bad = total = 0
+    for begin in (0, 511, 1023):
+        refs = O.run([O.System(64, T, n_paths=1024, path_begin=begin, path_count=1) for T in Ts], 0, 1)
+        for k in range(3):
+            total += 1
+            bad += int(np.max(np.abs(recs[k][begin][FIELDS] - refs[k][0][FIELDS])) > 1e-5)
+    assert bad <= 1, f"{bad} of {total} sampled paths differ"
+
+
+def test_stalled_bulk_copy_reports_timeout():
+    """Failure detection: a bulk copy that is never issued makes the bounded
+    mbarrier wait give up (about 2 s); the host reads MP_ETIMEOUT, the context
+    stays usable."""
+    sim = mp.Simulation([mp.System(8, 1.0, n_paths=1)], 1, 1, flags=mp.FLAG_STREAM | mp.FLAG_TEST_STALL)
+    sim.run()
+    with pytest.raises(mp.MPError) as ei:
+        sim.estimates(0)
+    assert ei.value.status == mp.MP_ETIMEOUT
+    sim.close()
+    # the device still works
+    with mp.Simulation([mp.System(8, 1.0, n_paths=4)], 1, 1, flags=mp.FLAG_STREAM) as ok:
+        ok.run()
+        assert np.isfinite(ok.estimates(0)["e"])
+
+
+def test_fp64_l64_does_not_fit_the_ring():
+    with pytest.raises(mp.MPError) as ei:
+        mp.Simulation([mp.System(64, 1.44, n_paths=1)], 1, 1, precision=mp.FP64)
+    assert ei.value.status == mp.MP_EINVAL
