@@ -1,19 +1,27 @@
 """Benchmark of the multipath Metropolis hot path on one node.
 
-A step is one full multipath run of the benchmark workload: simple cubic
-L=16 (4096 spins), J=1, h=0, 21 temperatures uniformly spaced in [0.5, 2.5],
-4096 independent paths per temperature, 2000 thermalisation + 2000
-measurement checkerboard sweeps, FP32 spins in shared memory with FP64
-accumulators, then the FP64 cross-path reduction.  Inputs are synthetic
-(random unit-spin lattices drawn from Philox inside the kernel).
+A step is one full multipath run of a workload: every path of every system
+from its random initial state through its thermalisation and measurement
+sweeps, then the FP64 cross-path reduction.  Inputs are synthetic (random
+unit-spin lattices drawn from Philox inside the kernels).  Workloads:
 
-value: spin-update attempts/s over all ranks (N x paths x sweeps x systems /
+  sc16     (default) simple cubic L=16 (4096 spins), J=1, h=0, 21 temperatures
+           uniformly spaced in [0.5, 2.5], 4096 paths per temperature,
+           2000 thermalisation + 2000 measurement sweeps, FP32 spins in shared
+           memory, FP64 accumulators.
+  large    simple cubic L=64 (262144 spins), T in {1.40, 1.44, 1.48}, 1024 paths
+           each, 500 + 1000 sweeps, FP32 spins streamed from HBM.
+  batched  uneven sizes in one persistent launch: L in {8,12,16,20,24,32} with
+           8192/4096/2048/1024/512/256 paths, T=1.44, 1000 + 1000 sweeps, FP32.
+  plain    simple cubic L=4, T=1.5, 256 paths, 1000 + 1000 sweeps, FP64.
+
+value: spin-update attempts/s over all ranks (sites x paths x sweeps /
 device time of the timed steps, max over ranks).  Each rank runs its own full
-workload (weak scaling; paths of different ranks use different seeds; no
-collective on the data path).
+workload (weak scaling; ranks use different seeds; no collective on the data
+path).
 
---impl reference times the FP64 CPU oracle (the reference arm of this
-project) on a bounded sample of the same workload on the host cores.
+--impl reference times the FP64 CPU oracle (this project's reference arm) on
+a bounded sample of the same workload on the host cores.
 """
 from __future__ import annotations
 
@@ -30,22 +38,46 @@ sys.path.insert(0, ROOT)
 
 METRIC = ("spin-update attempts/s and independent path samples/s at stated σ "
           "vs FP64 GPU form")
-L, N_T, PATHS, N_THERM, N_MEAS = 16, 21, 4096, 2000, 2000
-TEMPS = [0.5 + 2.0 * k / (N_T - 1) for k in range(N_T)]
-N_SITES = L ** 3
-SWEEPS = N_THERM + N_MEAS
-WORKLOAD = (f"simple cubic L={L} periodic, J=1, h=0, {N_T} temperatures in [0.5,2.5], "
-            f"{PATHS} paths per temperature, {N_THERM}+{N_MEAS} checkerboard sweeps, "
-            "FP32 spins in shared memory, FP64 accumulators and reduction")
-# Algorithmic lane operations of one Metropolis attempt on this path:
-# Philox4x32-10 40 (10 rounds x 2 wide multiplies + 2 three-input xors),
-# 3 uniforms 6, trial direction 9 (z, sqrt via rsqrt, phi, sin, cos, x, y),
-# own spin 3 loads, local field 33 (18 neighbour loads + 15 adds),
-# dE 8, accept 5 (scale, exp, two compares, select), store 3,
-# measurement 2 (about 4.5 on the half of the sweeps that measure).
+TEMPS21 = [0.5 + 2.0 * k / 20 for k in range(21)]
+
+WORKLOADS = {
+    "sc16": dict(
+        systems=[(16, T, 4096) for T in TEMPS21], n_therm=2000, n_meas=2000, precision="fp32",
+        bound="alu", cpu_paths=2, ref_paths=1, fp64_paths=64,
+        text=("simple cubic L=16 periodic, J=1, h=0, 21 temperatures in [0.5,2.5], 4096 paths per "
+              "temperature, 2000+2000 checkerboard sweeps, FP32 spins in shared memory, FP64 "
+              "accumulators and reduction")),
+    "large": dict(
+        systems=[(64, T, 1024) for T in (1.40, 1.44, 1.48)], n_therm=500, n_meas=1000,
+        precision="fp32", bound="hbm", cpu_paths=1, ref_paths=1, fp64_paths=0,
+        text=("simple cubic L=64 periodic, J=1, h=0, T in {1.40,1.44,1.48}, 1024 paths each, "
+              "500+1000 checkerboard sweeps, FP32 spins streamed from HBM through TMA-staged "
+              "half-plane buffers")),
+    "batched": dict(
+        systems=[(Lb, 1.44, P) for Lb, P in ((8, 8192), (12, 4096), (16, 2048), (20, 1024), (24, 512),
+                                             (32, 256))],
+        n_therm=1000, n_meas=1000, precision="fp32", bound="alu", cpu_paths=1, ref_paths=1,
+        fp64_paths=0,
+        text=("uneven sizes in one persistent launch: simple cubic L in {8,12,16,20,24,32} with "
+              "8192/4096/2048/1024/512/256 paths, T=1.44, J=1, h=0, 1000+1000 sweeps, FP32 spins, "
+              "FP64 reductions")),
+    "plain": dict(
+        systems=[(4, 1.5, 256)], n_therm=1000, n_meas=1000, precision="fp64", bound="alu",
+        cpu_paths=256, ref_paths=256, fp64_paths=0,
+        text=("plain method, FP64: simple cubic L=4, J=1, h=0, T=1.5, 256 paths, 1000+1000 "
+              "checkerboard sweeps")),
+}
+
+# Algorithmic lane operations of one Metropolis attempt (instruction-bound
+# kernels): Philox4x32-10 40 (10 rounds x 2 wide multiplies + 2 three-input
+# xors), 3 uniforms 6, trial direction 9 (z, sqrt via rsqrt, phi, sin, cos,
+# x, y), own spin 3 loads, local field 33 (18 neighbour loads + 15 adds), dE 8,
+# accept 5 (scale, exp, two compares, select), store 3, measurement 2 (about
+# 4.5 on the half of the sweeps that measure).
 OPS_PER_ATTEMPT = 109
-CPU_SAMPLE_PATHS = 2        # oracle paths per temperature in the CPU baseline
-REF_STEP_PATHS = 1          # oracle paths per temperature per reference-arm step
+# Algorithmic HBM bytes of one attempt when the lattice streams from HBM:
+# each spin is read once and written once per sweep, 3 components x 4 bytes.
+BYTES_PER_ATTEMPT_FP32 = 24
 
 
 def load_peaks():
@@ -56,16 +88,22 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def oracle_sample(paths_per_T: int, threads: int | None = None):
-    """Run the FP64 oracle on `paths_per_T` paths of every temperature; returns (attempts, seconds)."""
+def attempts_of(systems, sweeps, paths_override=None):
+    return sum(Ls ** 3 * (paths_override or P) * sweeps for Ls, _, P in systems)
+
+
+def oracle_sample(w, paths_per_system: int, threads: int | None = None):
+    """Run the FP64 oracle on the first paths of every system; returns (attempts, seconds)."""
     import oracle
 
     oracle.build()
-    systems = [oracle.System(L, T, n_paths=PATHS, path_begin=0, path_count=paths_per_T) for T in TEMPS]
+    systems = [oracle.System(Ls, T, n_paths=P, path_begin=0, path_count=min(paths_per_system, P))
+               for Ls, T, P in w["systems"]]
     t0 = time.perf_counter()
-    oracle.run(systems, N_THERM, N_MEAS, seed=1, threads=threads)
+    oracle.run(systems, w["n_therm"], w["n_meas"], seed=1, threads=threads)
     dt = time.perf_counter() - t0
-    return N_SITES * paths_per_T * N_T * SWEEPS, dt
+    att = sum(s.L ** 3 * s.path_count * (w["n_therm"] + w["n_meas"]) for s in systems)
+    return att, dt
 
 
 class ClockSampler:
@@ -118,26 +156,42 @@ def emit(obj):
     print(json.dumps(obj), flush=True)
 
 
-def run_reference(args, rank):
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The largest of every rank's x (the timed duration of the job)."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def job_throughput(units_per_rank: float, world: int, steps: int, total_ms: float) -> float:
+    """Weak scaling: every rank runs its own full workload; units/s of the whole job."""
+    return units_per_rank * world * steps / (total_ms / 1e3)
+
+
+def run_reference(args, w, rank):
     if rank != 0:
         return
     cores = os.cpu_count() or 1
     for _ in range(args.warmup):
-        oracle_sample(REF_STEP_PATHS, cores)
+        oracle_sample(w, w["ref_paths"], cores)
     total_att, total_s = 0, 0.0
     for _ in range(args.steps):
-        att, dt = oracle_sample(REF_STEP_PATHS, cores)
+        att, dt = oracle_sample(w, w["ref_paths"], cores)
         total_att += att
         total_s += dt
     value = total_att / total_s
-    sample = (f"{REF_STEP_PATHS} path per temperature x {N_T} temperatures x {SWEEPS} sweeps "
-              f"of L={L} per step (FP64 oracle, {cores} threads)")
+    sample = (f"{w['ref_paths']} path(s) of each of the {len(w['systems'])} systems, all "
+              f"{w['n_therm'] + w['n_meas']} sweeps, per step (FP64 oracle, {cores} threads)")
     emit({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "attempts/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": sample},
+        "config": {"workload": w["text"], "sample": sample},
         "cpu_baseline": {"value": value, "unit": "attempts/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "attempts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -150,20 +204,28 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sc16", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     # shorter runs of the same launch (for profiling captures only)
-    ap.add_argument("--n-therm", type=int, default=N_THERM)
-    ap.add_argument("--n-meas", type=int, default=N_MEAS)
+    ap.add_argument("--n-therm", type=int, default=None)
+    ap.add_argument("--n-meas", type=int, default=None)
     args = ap.parse_args()
+    w = dict(WORKLOADS[args.workload])
+    if args.n_therm is not None:
+        w["n_therm"] = args.n_therm
+    if args.n_meas is not None:
+        w["n_meas"] = args.n_meas
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
 
     if args.impl == "reference":
-        run_reference(args, rank)
+        run_reference(args, w, rank)
         return
+
+    import ctypes
 
     import torch
 
@@ -186,10 +248,12 @@ def main():
         torch.cuda.synchronize(dev)
 
     seed = 1 + rank
-    n_therm, n_meas = args.n_therm, args.n_meas
+    n_therm, n_meas = w["n_therm"], w["n_meas"]
     sweeps = n_therm + n_meas
-    systems = [mp.System(L, T, n_paths=PATHS) for T in TEMPS]
-    sim = mp.Simulation(systems, n_therm, n_meas, seed=seed, precision=mp.FP32, device=dev)
+    precision = mp.FP64 if w["precision"] == "fp64" else mp.FP32
+    systems = [mp.System(Ls, T, n_paths=P) for Ls, T, P in w["systems"]]
+    n_sys = len(systems)
+    sim = mp.Simulation(systems, n_therm, n_meas, seed=seed, precision=precision, device=dev)
     stream = sim.stream
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
@@ -219,89 +283,91 @@ def main():
     barrier()
     clk = clocks.stop()
 
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
-    attempts_rank = N_SITES * PATHS * N_T * sweeps
-    value = attempts_rank * world * args.steps / (total_ms / 1e3)
-    paths_per_s = PATHS * N_T * world * args.steps / (total_ms / 1e3)
-    ests = [sim.estimates(k) for k in range(N_T)]
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
+    attempts_rank = attempts_of(w["systems"], sweeps)
+    paths_rank = sum(P for _, _, P in w["systems"])
+    value = job_throughput(attempts_rank, world, args.steps, total_ms)
+    paths_per_s = job_throughput(paths_rank, world, args.steps, total_ms)
+    ests = [sim.estimates(k) for k in range(n_sys)]
 
     # end to end through the public API: create (system and work tables H2D),
     # run, read every system's estimates (D2H), destroy -- all inside the clock
     e2e_s = []
-    import ctypes
-
-    h2d = ctypes.sizeof(mp.MPSystem) * N_T  # the caller's system table
     for k in range(max(1, min(2, args.steps))):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        with mp.Simulation(systems, n_therm, n_meas, seed=seed + 1000 * (k + 1), device=dev) as s2:
+        with mp.Simulation(systems, n_therm, n_meas, seed=seed + 1000 * (k + 1), precision=precision,
+                           device=dev) as s2:
             s2.run()
-            for j in range(N_T):
+            for j in range(n_sys):
                 s2.estimates(j)
             plan = s2.plan()
         e2e_s.append(time.perf_counter() - t0)
-    # the library uploads its DevSystem (80 B) and WorkItem (16 B) tables too
-    h2d_total = h2d + 80 * N_T + 16 * plan["n_items"] + 8 * N_T
-    d2h_total = ctypes.sizeof(mp.MPEstimates) * N_T
+    # the caller's system table, then the library's DevSystem (88 B), WorkItem
+    # (16 B) and spin-offset (8 B) tables
+    h2d_total = (ctypes.sizeof(mp.MPSystem) + 88 + 8) * n_sys + 16 * plan["n_items"]
+    d2h_total = ctypes.sizeof(mp.MPEstimates) * n_sys
     e2e_value = attempts_rank * world / (sum(e2e_s) / len(e2e_s))
 
     peaks, peak_kind = load_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    n_sm = props.multi_processor_count
-    peak_ops = n_sm * 128 * sm_max * 1e6 / 1e12  # lane-ops/s in units of 1e12
     sweep_avg = sum(sweep_ms) / len(sweep_ms)
-    achieved = OPS_PER_ATTEMPT * attempts_rank / (sweep_avg / 1e3) / 1e12
+    kernel_rate = attempts_rank / (sweep_avg / 1e3)
+    n_sm = props.multi_processor_count
+    if w["bound"] == "hbm":
+        peak = float(peaks["hbm_gbs"])
+        achieved = BYTES_PER_ATTEMPT_FP32 * kernel_rate / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "bytes_per_attempt": BYTES_PER_ATTEMPT_FP32,
+                "peak_basis": f"{peak_kind} HBM copy bandwidth"}
+    else:
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = n_sm * 128 * sm_max * 1e6 / 1e12  # lane-ops/s in units of 1e12
+        achieved = OPS_PER_ATTEMPT * kernel_rate / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                "traffic": None, "ops_per_attempt": OPS_PER_ATTEMPT,
+                "peak_basis": f"{n_sm} SMs x 128 lanes x {sm_max:.0f} MHz ({peak_kind} max clock)"}
+    roof.update(kernel="sweep_kernel", sweep_ms=sweep_avg, reduce_ms=sum(reduce_ms) / len(reduce_ms))
 
     fp64 = None
-    if not args.no_fp64:
-        sub = 64
-        with mp.Simulation([mp.System(L, T, n_paths=sub) for T in TEMPS], n_therm, n_meas, seed=seed,
-                           precision=mp.FP64, device=dev) as s64:
+    if w["fp64_paths"] and not args.no_fp64 and precision == mp.FP32:
+        sub = w["fp64_paths"]
+        with mp.Simulation([mp.System(Ls, T, n_paths=sub) for Ls, T, _ in w["systems"]], n_therm, n_meas,
+                           seed=seed, precision=mp.FP64, device=dev) as s64:
             s64.run()
             torch.cuda.synchronize(dev)
             a64, _ = s64.timing()
-            e64 = [s64.estimates(k) for k in range(N_T)]
-        att64 = N_SITES * sub * N_T * sweeps
-        v64 = att64 / (a64 / 1e3)
+            e64 = [s64.estimates(k) for k in range(n_sys)]
+        v64 = attempts_of(w["systems"], sweeps, sub) / (a64 / 1e3)
         worst = max(abs(ests[k]["e"] - e64[k]["e"]) / (ests[k]["e_se"] ** 2 + e64[k]["e_se"] ** 2) ** 0.5
-                    for k in range(N_T))
-        fp64 = {"value": v64, "unit": "attempts/s", "sample": f"{sub} paths per temperature, same sweeps",
-                "fp32_over_fp64": (attempts_rank / (sweep_avg / 1e3)) / v64,
-                "max_e_diff_in_combined_se": worst}
+                    for k in range(n_sys))
+        fp64 = {"value": v64, "unit": "attempts/s", "sample": f"{sub} paths per system, same sweeps",
+                "fp32_over_fp64": kernel_rate / v64, "max_e_diff_in_combined_se": worst}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
-        att, dt = oracle_sample(CPU_SAMPLE_PATHS, cores)
+        att, dt = oracle_sample(w, w["cpu_paths"], cores)
         cpu = {"value": att / dt, "unit": "attempts/s", "cores": cores, "kind": "oracle",
-               "sample": f"{CPU_SAMPLE_PATHS} paths per temperature x {N_T} temperatures x {SWEEPS} sweeps "
-                         f"of L={L} ({att:.3g} attempts, {dt:.1f} s)"}
+               "sample": f"{w['cpu_paths']} path(s) of each of the {n_sys} systems, all {sweeps} sweeps "
+                         f"({att:.3g} attempts, {dt:.1f} s)"}
 
     if rank == 0:
         emit({
             "metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD, "L": L, "temperatures": N_T, "paths_per_temperature": PATHS,
-                       "n_therm": n_therm, "n_meas": n_meas, "parallelism": f"replicas x{world}",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if precision == mp.FP64 else "f32", "data": "synthetic",
+            "config": {"workload": w["text"], "name": args.workload, "n_therm": n_therm, "n_meas": n_meas,
+                       "systems": len(systems), "paths": paths_rank, "parallelism": f"replicas x{world}",
                        "l2": "flushed between timed steps (256 MB write)", "plan": sim.plan()},
             "paths_per_s": paths_per_s,
             "sigma": {"e_se_max": max(e["e_se"] for e in ests), "m_se_max": max(e["m_se"] for e in ests),
-                      "e_at_T": {f"{TEMPS[k]:.1f}": [ests[k]["e"], ests[k]["e_se"]] for k in (0, 10, 20)}},
+                      "e": [[e["T"], e["e"], e["e_se"]] for e in ests[:: max(1, n_sys // 3)]]},
             "fp64_form": fp64,
             "e2e": {"value": e2e_value, "unit": "attempts/s", "h2d_bytes_per_step": h2d_total,
                     "d2h_bytes_per_step": d2h_total},
             "gpu_launches": 2 * args.steps,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
-                         "frac": achieved / peak_ops, "traffic": None,
-                         "kernel": "sweep_kernel<float>", "ops_per_attempt": OPS_PER_ATTEMPT,
-                         "peak_basis": f"{n_sm} SMs x 128 lanes x {sm_max:.0f} MHz ({peak_kind} max clock)",
-                         "sweep_ms": sweep_avg, "reduce_ms": sum(reduce_ms) / len(reduce_ms)},
+            "roofline": roof,
             "cpu_baseline": cpu,
             "clocks": clk,
         })

@@ -847,13 +847,13 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
   meter.finish(P.n_meas);
   group_sync(tp, bar);
 
-  double worst = 0.0;
+  Real worst = Real(0);  // in the working precision: FP64 runs at 1/64 rate on this GPU
   for (int i = tid; i < N; i += tp) {
     const int x = i % L, y = (i / L) % L, z = i / (L * L);
     const Real* hpl = plane(z, (x + y + z) & 1);
     const int hp = (x >> 1) + HL * y;
-    const double a = hpl[hp], b = hpl[HP + hp], c = hpl[2 * HP + hp];
-    worst = fmax(worst, fabs(sqrt(a * a + b * b + c * c) - 1.0));
+    const Real a = hpl[hp], b = hpl[HP + hp], c = hpl[2 * HP + hp];
+    worst = fmax(worst, fabs(sqrt(a * a + b * b + c * c) - Real(1)));
     if (P.spins != nullptr) {
       double* out = P.spins + P.spin_offset[sys_idx] + path * 3 * static_cast<int64_t>(N);
       out[3 * i + 0] = a;
@@ -861,8 +861,8 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
       out[3 * i + 2] = c;
     }
   }
-  meter.write_record(P.records + (sy.rec_offset + path) * MP_NREC, accepted, worst, nsweeps,
-                     P.n_meas, N, tp, bar);
+  meter.write_record(P.records + (sy.rec_offset + path) * MP_NREC, accepted,
+                     static_cast<double>(worst), nsweeps, P.n_meas, N, tp, bar);
   group_sync(tp, bar);  // the slice and the HBM buffer are reused by the next item
 }
 
