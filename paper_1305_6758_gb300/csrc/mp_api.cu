@@ -68,7 +68,9 @@ int round_up(int v, int m) { return (v + m - 1) / m * m; }
 int half_plane_bytes(int L, int real) { return round_up(3 * (L * L / 2) * real, 16); }
 
 bool streamed(const mp_system& s, int precision, uint32_t flags) {
-  return s.lattice == MP_LATTICE_SC && ((flags & MP_FLAG_STREAM) || !sweep_supports_L(precision, s.L));
+  // the plane wavefront needs at least four planes
+  return s.lattice == MP_LATTICE_SC && s.L >= 4 &&
+         ((flags & MP_FLAG_STREAM) || !sweep_supports_L(precision, s.L));
 }
 
 }  // namespace
@@ -252,7 +254,7 @@ int plan(mp_state* h, const mp_config* cfg) {
       tp[k] = t;
       ring[k] = 16;
       auto need = [&]() {
-        return round_up(slice_spin_offset(t, ring[k]) + 128 + 8 * half_plane_bytes(L, real), 128);
+        return round_up(slice_spin_offset(t, ring[k]) + 128 + 9 * half_plane_bytes(L, real), 128);
       };
       slice[k] = need();
       while (ring[k] > 1 && slice[k] > smem_max) {

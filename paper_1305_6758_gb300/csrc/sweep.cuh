@@ -204,7 +204,8 @@ struct Partials {
 // spin, energy change from the local field, acceptance test.
 template <typename Real, bool kMeas, bool kEnergy>
 __device__ __forceinline__ void update(uint32_t i, uint32_t sweep, uint32_t c2, uint32_t c3,
-                                       const PhiloxKeys& key, Real* own, int S, int hh, Real hx,
+                                       const PhiloxKeys& key, Real* __restrict__ own, int S, int hh,
+                                       Real hx,
                                        Real hy, Real hz, Real J, Real hf, Real bp, int& accepted,
                                        Partials<Real>& part) {
   using A = Arith<Real>;
@@ -603,9 +604,12 @@ __device__ __forceinline__ void tma_store(void* dst, const void* src, uint32_t b
                : "memory");
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
-__device__ __forceinline__ void tma_wait_read_all_but_last() {
-  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+// Wait until at most N (a constant) bulk store groups may still read shared memory.
+template <int N>
+__device__ __forceinline__ void tma_wait_read_n() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
 }
+#define tma_wait_read(n) tma_wait_read_n<n>()
 __device__ __forceinline__ void tma_wait_all() {
   asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
@@ -648,7 +652,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
 // Lattices too large for shared memory.  Each path's spins stay in HBM in the
 // layout [z][colour][component][L*L/2] (a "half-plane" is one colour of one
 // z-plane, padded to 16 bytes), in a buffer owned by the thread group for the
-// whole run.  A sweep walks the z-planes as a wavefront over a ring of 4 + 4
+// whole run.  A sweep walks the z-planes as a wavefront over a ring of 4 + 5
 // half-plane buffers in shared memory, filled by TMA bulk copies and written
 // back by bulk stores:
 //   step q = 0 .. L+1:  (a) colour-0 update of plane q          (q < L)
@@ -660,7 +664,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
 // sees exactly the neighbour values of the two-pass checkerboard sweep.
 // Ring indices: colour-0 step index q' = 0..L+1 (planes 0..L-1, 0, 1) in slot
 // q' mod 4; colour-1 step index q' = -1..L (planes L-1, 0..L-1, 0) in slot
-// (q'+1) mod 4.  Loads run 1-2 steps ahead of use.
+// (q'+1) mod 5.  Every load is issued two steps before its first use.
+constexpr int kSlots = 9;  // half-plane buffers per streamed path: 4 for colour 0, 5 for colour 1
+
 template <typename Real>
 struct StreamLayout {
   static __host__ __device__ int hps(int L) {  // padded half-plane, in Reals
@@ -677,15 +683,15 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
   const int L = sy.L, HL = L / 2, HP = L * L / 2;
   const int hps = StreamLayout<Real>::hps(L);
   const uint32_t bytes = static_cast<uint32_t>(hps * sizeof(Real));
-  // [8 mbarriers][8 load counters] in 128 bytes, then the 8 half-plane buffers
+  // [9 mbarriers][9 load counters] in 128 bytes, then the 9 half-plane buffers
   uint64_t* mbar = reinterpret_cast<uint64_t*>(slice + slice_spin_offset(tp, sy.ring));
-  uint32_t* issued = reinterpret_cast<uint32_t*>(mbar + 8);
+  uint32_t* issued = reinterpret_cast<uint32_t*>(mbar + kSlots);
   Real* buf = reinterpret_cast<Real*>(slice + slice_spin_offset(tp, sy.ring) + 128);
-  // buffer of colour c, step index q (see above)
-  auto c0buf = [&](int q) { return buf + ((q & 3)) * hps; };
-  auto c1buf = [&](int q) { return buf + (4 + ((q + 1) & 3)) * hps; };
+  // buffer of colour c, step index q (see above): 4 slots for colour 0, 5 for colour 1
+  auto c0buf = [&](int q) { return buf + (q & 3) * hps; };
+  auto c1buf = [&](int q) { return buf + (4 + (q + 1) % 5) * hps; };
   auto c0bar = [&](int q) { return mbar + (q & 3); };
-  auto c1bar = [&](int q) { return mbar + 4 + ((q + 1) & 3); };
+  auto c1bar = [&](int q) { return mbar + 4 + (q + 1) % 5; };
   auto plane = [&](int z, int c) { return lat + (static_cast<int64_t>(z) * 2 + c) * hps; };
   auto wrap = [&](int q) { return ((q % L) + L) % L; };
   const uint32_t c2 = static_cast<uint32_t>(path);
@@ -718,7 +724,7 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
   if (tid < kAccDoubles) meter.acc[tid] = 0.0;
   if (tid == 0) abort_flag[gidx] = 0;
   if (producer) {
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < kSlots; ++k) {
       mbar_init(mbar + k, 1);
       issued[k] = 0;
     }
@@ -735,8 +741,9 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
   const bool active = tid < HL * RS;
   const int hx = active ? tid % HL : 0;
   const int y0 = active ? tid / HL : L;
-  // loads per sweep into each ring slot, for the mbarrier phase parity
-  auto per_sweep = [&](int j) { return (L + 1 - j) / 4 + 1; };
+  // loads per sweep into each ring slot, for the mbarrier phase parity: slot
+  // j of a ring of n slots takes the shifted step indices j, j + n, ... <= L+1
+  auto per_sweep = [&](int j, int n) { return (L + 1 - j) / n + 1; };
   int accepted = 0;
   const int64_t nsweeps = P.n_therm + P.n_meas;
   bool ok = true;
@@ -747,30 +754,49 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
     const int64_t j = s - P.n_therm;
     Partials<Real> part{Real(0), Real(0), Real(0), Real(0)};
     auto parity0 = [&](int q) {
-      return static_cast<uint32_t>((s * per_sweep(q & 3) + q / 4) & 1);
+      return static_cast<uint32_t>((s * per_sweep(q & 3, 4) + q / 4) & 1);
     };
     auto parity1 = [&](int q) {
       const int qq = q + 1;
-      return static_cast<uint32_t>((s * per_sweep(qq & 3) + qq / 4) & 1);
+      return static_cast<uint32_t>((s * per_sweep(qq % 5, 5) + qq / 5) & 1);
+    };
+    // Buffers first used at step q: colour-0 index q, colour-1 index q+1 (at
+    // q = 0 also colour-1 indices -1 and 0).  Only the producer waits on their
+    // mbarriers; the group barrier after the wait hands the data to everyone.
+    auto wait_step = [&](int q) {
+      bool w = mbar_wait(c0bar(q), parity0(q), P.error);
+      if (q == 0) {
+        w = w && mbar_wait(c1bar(-1), parity1(-1), P.error);
+        w = w && mbar_wait(c1bar(0), parity1(0), P.error);
+      }
+      if (q < L) w = w && mbar_wait(c1bar(q + 1), parity1(q + 1), P.error);
+      if (!w) abort_flag[gidx] = 1;
     };
     if (producer) {
       tma_wait_all();  // the previous sweep's write-backs are complete
       if (!(P.test_stall && s == 0)) load(c0buf(0), plane(0, 0), 0);
       load(c0buf(1), plane(1 % L, 0), 1);
-      load(c1buf(-1), plane(L - 1, 1), 4);
-      load(c1buf(0), plane(0, 1), 5);
-      load(c1buf(1), plane(1 % L, 1), 6);
+      for (int q1 = -1; q1 <= 2; ++q1) load(c1buf(q1), plane(wrap(q1), 1), 4 + (q1 + 1) % 5);
+      wait_step(0);
     }
-    // One colour phase over plane z: own, same-plane, +z and -z buffers.
-    auto phase = [&](int c, int z, Real* own, const Real* same, const Real* up, const Real* dn,
-                     bool energy) {
+    group_sync(tp, bar);
+    if (abort_flag[gidx]) {
+      ok = false;
+      break;
+    }
+    // One colour phase over plane z: own, same-plane, +z and -z buffers.  The
+    // thread's column hx is fixed, so its +-x offsets for either parity of x
+    // are too (oxp1: +x when x is odd, oxm0: -x when x is even).
+    const int oxp1 = (hx == HL - 1) ? -(HL - 1) : 1;
+    const int oxm0 = (hx == 0) ? (HL - 1) : -1;
+    auto phase = [&](int c, int z, Real* __restrict__ own, const Real* __restrict__ same,
+                     const Real* __restrict__ up, const Real* __restrict__ dn, bool energy) {
+#pragma unroll 4
       for (int y = y0; y < L; y += RS) {
         const int hp = hx + HL * y;
         const int p = (y + z + c) & 1;
-        const int x = 2 * hx + p;
-        const int row = HL * y;
-        const int xp = row + ((x + 1 == L) ? 0 : ((x + 1) >> 1));
-        const int xm = row + ((x == 0) ? ((L - 1) >> 1) : ((x - 1) >> 1));
+        const int xp = hp + (p ? oxp1 : 0);
+        const int xm = hp + (p ? 0 : oxm0);
         const int yp = (y == L - 1) ? hp - (L - 1) * HL : hp + HL;
         const int ym = (y == 0) ? hp + (L - 1) * HL : hp - HL;
         Real f[3];
@@ -795,16 +821,11 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
       }
     };
     for (int q = 0; q <= L + 1; ++q) {
-      // wait for the buffers first used at this step
-      bool w = mbar_wait(c0bar(q), parity0(q), P.error);
-      if (q == 0) {
-        w = w && mbar_wait(c1bar(-1), parity1(-1), P.error);
-        w = w && mbar_wait(c1bar(0), parity1(0), P.error);
-      }
-      if (q < L) w = w && mbar_wait(c1bar(q + 1), parity1(q + 1), P.error);
-      if (!w) abort_flag[gidx] = 1;
       if (q < L) phase(0, q, c0buf(q), c1buf(q), c1buf(q + 1), c1buf(q - 1), false);
       fence_async_shared();
+      // the buffers step q+1 starts with were issued at step q-1: the producer
+      // confirms them now, and the barrier below hands them to every thread
+      if (producer && q + 1 <= L + 1) wait_step(q + 1);
       group_sync(tp, bar);
       if (abort_flag[gidx]) {
         ok = false;
@@ -815,13 +836,16 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
       if (q >= 2) phase(1, wrap(q - 1), c1buf(q - 1), c0buf(q - 1), c0buf(q), c0buf(q - 2), meas);
       fence_async_shared();
       group_sync(tp, bar);
-      if (producer) {
+      if (producer) {  // after the barrier: the buffers just written are complete
         if (q >= 2) tma_store(plane(wrap(q - 1), 1), c1buf(q - 1), bytes);
-        tma_wait_read_all_but_last();
+        // the slots refilled now last held colour-0 index q-2 (stored at step
+        // q-2) and colour-1 index q-2 (stored at step q-1): all but the two
+        // newest store groups must have finished reading shared memory
+        tma_wait_read(2);
         // colour-0 step indices L and L+1 reload planes 0 and 1 written this sweep
         if (q + 2 >= L) tma_wait_all();
         if (q + 2 <= L + 1) load(c0buf(q + 2), plane(wrap(q + 2), 0), (q + 2) & 3);
-        if (q + 2 <= L) load(c1buf(q + 2), plane(wrap(q + 2), 1), 4 + ((q + 3) & 3));
+        if (q + 3 <= L) load(c1buf(q + 3), plane(wrap(q + 3), 1), 4 + (q + 4) % 5);
       }
     }
     if (!ok) break;
@@ -834,13 +858,13 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
     if (!ok) {
       // a load did not arrive in time: wait (bounded) for every load still
       // in flight before the shared memory is given up
-      for (int k = 0; k < 8; ++k)
+      for (int k = 0; k < kSlots; ++k)
         if (issued[k] > 0) mbar_wait(mbar + k, (issued[k] - 1) & 1, P.error);
     }
     tma_wait_all();
     fence_async_global();
     // every consumer passed its last wait before the last barrier
-    for (int k = 0; k < 8; ++k) mbar_inval(mbar + k);
+    for (int k = 0; k < kSlots; ++k) mbar_inval(mbar + k);
   }
   group_sync(tp, bar);
   if (!ok) return;  // the error flag is set; the path's record is not written
