@@ -253,7 +253,8 @@ def main():
     precision = mp.FP64 if w["precision"] == "fp64" else mp.FP32
     systems = [mp.System(Ls, T, n_paths=P) for Ls, T, P in w["systems"]]
     n_sys = len(systems)
-    sim = mp.Simulation(systems, n_therm, n_meas, seed=seed, precision=precision, device=dev)
+    tune = mp.FLAG_AUTOTUNE
+    sim = mp.Simulation(systems, n_therm, n_meas, seed=seed, precision=precision, device=dev, flags=tune)
     stream = sim.stream
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
@@ -297,7 +298,7 @@ def main():
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         with mp.Simulation(systems, n_therm, n_meas, seed=seed + 1000 * (k + 1), precision=precision,
-                           device=dev) as s2:
+                           device=dev, flags=tune) as s2:
             s2.run()
             for j in range(n_sys):
                 s2.estimates(j)
@@ -359,7 +360,8 @@ def main():
             "dtype": "f64" if precision == mp.FP64 else "f32", "data": "synthetic",
             "config": {"workload": w["text"], "name": args.workload, "n_therm": n_therm, "n_meas": n_meas,
                        "systems": len(systems), "paths": paths_rank, "parallelism": f"replicas x{world}",
-                       "l2": "flushed between timed steps (256 MB write)", "plan": sim.plan()},
+                       "l2": "flushed between timed steps (256 MB write)", "plan": sim.plan(),
+                       "autotuned": [sim.system_plan(k) for k in sorted({0, n_sys // 2, n_sys - 1})]},
             "paths_per_s": paths_per_s,
             "sigma": {"e_se_max": max(e["e_se"] for e in ests), "m_se_max": max(e["m_se"] for e in ests),
                       "e": [[e["T"], e["e"], e["e_se"]] for e in ests[:: max(1, n_sys // 3)]]},

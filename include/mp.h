@@ -66,6 +66,11 @@ extern "C" {
 #define MP_FLAG_STREAM 4u     /* stream every simple-cubic lattice from HBM, even
                                  those that fit in shared memory (lattices too
                                  large for shared memory are always streamed) */
+#define MP_FLAG_AUTOTUNE 8u   /* at create, time a few threads-per-path layouts of
+                                 each system in the batch's own kernel (one
+                                 wave of its work items, ~2e8 attempts each)
+                                 and keep the fastest; ignored when
+                                 threads_per_path is set */
 #define MP_FLAG_TEST_STALL 0x100u /* failure injection for tests: streamed paths
                                      never issue their first bulk copy, so the
                                      kernel's bounded wait runs out (about 2 s)
@@ -250,6 +255,12 @@ int mp_timing(mp_handle h, double* sweep_ms, double* reduce_ms);
  * grid, dynamic shared memory bytes per CTA, work items.  Any output may be
  * NULL. */
 int mp_plan(mp_handle h, int* cta_threads, int* grid, int* smem_bytes, int* n_items);
+
+/* Launch shape of one system: threads per path, paths per CTA, and whether
+ * its lattice is streamed from HBM (1) or held in shared memory (0).  Any
+ * output may be NULL.  Errors: MP_EINVAL (bad index). */
+int mp_system_plan(mp_handle h, int system, int* threads_per_path, int* paths_per_cta,
+                   int* streamed_from_hbm);
 
 /* Philox4x32-10 of n counters: d_ctr holds 4n uint32 words (c0 c1 c2 c3 per
  * counter), d_out receives 4n words.  Device pointers, caller-owned; queued

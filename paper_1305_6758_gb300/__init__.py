@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(_HERE, "libmp.so")
 SC, CHAIN = 0, 1
 FP32, FP64 = 0, 1
 INIT_SPHERE, INIT_ANGLES, INIT_ORDERED = 0, 1, 2
-FLAG_GRAPH, FLAG_KEEP_SPINS, FLAG_STREAM, FLAG_TEST_STALL = 1, 2, 4, 0x100
+FLAG_GRAPH, FLAG_KEEP_SPINS, FLAG_STREAM, FLAG_AUTOTUNE, FLAG_TEST_STALL = 1, 2, 4, 8, 0x100
 
 MP_OK, MP_EINVAL, MP_ENOMEM, MP_ECUDA, MP_ESTATE, MP_ECANCELED, MP_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 
@@ -97,7 +97,8 @@ assert ctypes.sizeof(MPEstimates) == NEST * 8
 # Every symbol include/mp.h declares.
 EXPORTS = [
     "mp_create", "mp_create_ex", "mp_run", "mp_set_seed", "mp_estimates", "mp_paths",
-    "mp_device_buffers", "mp_spins", "mp_backward", "mp_timing", "mp_plan", "mp_philox",
+    "mp_device_buffers", "mp_spins", "mp_backward", "mp_timing", "mp_plan", "mp_system_plan",
+    "mp_philox",
     "mp_destroy", "mp_last_error", "mp_status_string",
 ]
 
@@ -128,6 +129,7 @@ def load_library(path: str = LIB_PATH):
     lib.mp_backward.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.mp_timing.argtypes = [H, P(dbl), P(dbl)]
     lib.mp_plan.argtypes = [H] + [P(ctypes.c_int)] * 4
+    lib.mp_system_plan.argtypes = [H, ctypes.c_int] + [P(ctypes.c_int)] * 3
     lib.mp_philox.argtypes = [ctypes.c_void_p, i64, u64, ctypes.c_void_p, ctypes.c_void_p]
     for name in EXPORTS:
         getattr(lib, name).restype = ctypes.c_int
@@ -317,6 +319,11 @@ class Simulation:
         v = [ctypes.c_int() for _ in range(4)]
         _check(_lib.mp_plan(self._h, *[ctypes.byref(x) for x in v]), self._h)
         return dict(cta_threads=v[0].value, grid=v[1].value, smem_bytes=v[2].value, n_items=v[3].value)
+
+    def system_plan(self, system: int) -> dict:
+        v = [ctypes.c_int() for _ in range(3)]
+        _check(_lib.mp_system_plan(self._h, system, *[ctypes.byref(x) for x in v]), self._h)
+        return dict(threads_per_path=v[0].value, paths_per_cta=v[1].value, streamed=bool(v[2].value))
 
 
 def _wrap_device(ptr: int, shape, device):

@@ -106,6 +106,8 @@ struct mp_state {
   int64_t* d_spin_offset = nullptr;
   int* d_error = nullptr;          // nonzero when a bounded wait in a kernel gave up
   void* d_lattice = nullptr;       // HBM lattices of streamed paths
+  size_t lattice_capacity = 0;     // bytes allocated at d_lattice
+  std::vector<int> tp_override;    // per system threads per path (autotuner), 0 = planner
   int64_t lattice_stride = 0;      // bytes per (CTA, group) lattice buffer
   int lattice_groups = 0;          // buffers per CTA
   std::vector<void*> owned;
@@ -163,6 +165,18 @@ void* dev_alloc(mp_state* h, size_t bytes) {
   }
   if (p) h->owned.push_back(p);
   return p;
+}
+
+void dev_free(mp_state* h, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < h->owned.size(); ++i) {
+    if (h->owned[i] == p) {
+      h->owned.erase(h->owned.begin() + static_cast<long>(i));
+      break;
+    }
+  }
+  if (h->alloc_fn) h->free_fn(h->alloc_ctx, p);
+  else cudaFree(p);
 }
 
 void release(mp_state* h) {
@@ -223,6 +237,9 @@ int validate(const mp_config* cfg) {
 int plan(mp_state* h, const mp_config* cfg) {
   const int real = h->precision == MP_FP64 ? 8 : 4;
   const int n = static_cast<int>(h->systems.size());
+  h->lattice_groups = 0;
+  h->lattice_stride = 0;
+  h->max_paths = 0;
   // one kernel per lattice size when the batch has a single size; lattices
   // too large for shared memory are streamed from HBM (any size, one kernel)
   auto variant_of = [&](const mp_system& sy) {
@@ -244,7 +261,8 @@ int plan(mp_state* h, const mp_config* cfg) {
   for (int k = 0; k < n; ++k) {
     const int64_t N = sites_of(h->systems[k]);
     const int NH = static_cast<int>((N + 1) / 2);
-    int t = cfg->threads_per_path;
+    int t = (static_cast<int>(h->tp_override.size()) > k && h->tp_override[k] > 0) ? h->tp_override[k]
+                                                                                  : cfg->threads_per_path;
     if (streamed(h->systems[k], h->precision, h->flags)) {
       // one thread per column x/2 of a z-plane and about L/4 rows per thread
       const int L = h->systems[k].L, HL = L / 2;
@@ -412,6 +430,139 @@ int enqueue_run(mp_state* h) {
 
 }  // namespace
 
+// The HBM lattice buffers of the current plan (streamed paths), grown on demand.
+int ensure_lattice(mp_state* h) {
+  if (h->lattice_groups == 0) return MP_OK;
+  h->lattice_stride = (h->lattice_stride + 255) / 256 * 256;
+  const size_t need = static_cast<size_t>(h->grid) * h->lattice_groups * h->lattice_stride;
+  if (need <= h->lattice_capacity) return MP_OK;
+  MP_CUDA(h, cudaStreamSynchronize(h->stream));
+  dev_free(h, h->d_lattice);
+  h->d_lattice = dev_alloc(h, need);
+  h->lattice_capacity = h->d_lattice ? need : 0;
+  if (!h->d_lattice) return fail(h, MP_ENOMEM, "lattice buffer allocation failed");
+  return MP_OK;
+}
+
+int upload_tables(mp_state* h, const std::vector<WorkItem>& items) {
+  const int n = static_cast<int>(h->hsys.size());
+  MP_CUDA(h, cudaMemcpyAsync(h->d_sys, h->hsys.data(), sizeof(DevSystem) * n, cudaMemcpyHostToDevice,
+                             h->stream));
+  MP_CUDA(h, cudaMemcpyAsync(h->d_items, items.data(), sizeof(WorkItem) * items.size(),
+                             cudaMemcpyHostToDevice, h->stream));
+  MP_CUDA(h, cudaMemcpyAsync(h->d_spin_offset, h->spin_offset.data(), sizeof(int64_t) * n,
+                             cudaMemcpyHostToDevice, h->stream));
+  MP_CUDA(h, cudaStreamSynchronize(h->stream));
+  return MP_OK;
+}
+
+// Throughput (attempts per ms) of system k under the current plan: one wave
+// of its work items through the real sweep kernel, with enough sweeps for
+// about 2e8 attempts.  Returns < 0 on error.
+double calibrate(mp_state* h, int k) {
+  std::vector<WorkItem> sub;
+  int64_t paths = 0;
+  for (const WorkItem& it : h->items) {
+    if (it.sys != k) continue;
+    sub.push_back(it);
+    paths += it.count;
+    if (static_cast<int>(sub.size()) >= h->grid) break;
+  }
+  if (sub.empty() || upload_tables(h, sub) != MP_OK || ensure_lattice(h) != MP_OK) return -1.0;
+  const double per_sweep = static_cast<double>(paths) * h->hsys[k].N;
+  const int64_t sweeps = std::max<int64_t>(2, std::min<int64_t>(512, static_cast<int64_t>(2e8 / per_sweep)));
+  SweepParams p{};
+  p.systems = h->d_sys;
+  p.items = h->d_items;
+  p.queue = h->d_queue;
+  p.records = h->d_rec;
+  p.n_items = static_cast<int32_t>(sub.size());
+  p.init_mode = h->init_mode;
+  p.n_therm = sweeps - 1;
+  p.n_meas = 1;
+  p.key = philox_round_keys(h->seed);
+  p.lattice = h->d_lattice;
+  p.lattice_stride = h->lattice_stride;
+  p.lattice_groups = h->lattice_groups;
+  p.error = h->d_error;
+  float ms = 0.f;
+  if (cudaMemsetAsync(h->d_queue, 0, sizeof(int), h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->d_error, 0, sizeof(int), h->stream) != cudaSuccess ||
+      cudaEventRecord(h->ev[0], h->stream) != cudaSuccess ||
+      launch_sweep(h->precision, h->variant, p, std::min<int>(h->grid, static_cast<int>(sub.size())),
+                   h->cta, h->smem, h->stream) != cudaSuccess ||
+      cudaEventRecord(h->ev[1], h->stream) != cudaSuccess ||
+      cudaEventSynchronize(h->ev[1]) != cudaSuccess ||
+      cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]) != cudaSuccess) {
+    cudaGetLastError();
+    return -1.0;
+  }
+  return per_sweep * sweeps / std::max(ms, 1e-3f);
+}
+
+// Threads-per-path candidates of system k for the autotuner.
+std::vector<int> tp_candidates(mp_state* h, int k, int cta_max) {
+  const mp_system& sy = h->systems[k];
+  std::vector<int> c;
+  auto add = [&](int t) {
+    t = round_up(std::max(t, 32), 32);
+    if (t <= cta_max && std::find(c.begin(), c.end(), t) == c.end()) c.push_back(t);
+  };
+  const int64_t N = sites_of(sy);
+  const int NH = static_cast<int>((N + 1) / 2);
+  if (streamed(sy, h->precision, h->flags)) {
+    const int HL = sy.L / 2;
+    for (int r : {2, 4, 8}) add(std::max(HL, HL * ((sy.L + r - 1) / r)));
+    return c;
+  }
+  if (sy.lattice == MP_LATTICE_SC) {
+    const int HP = sy.L * sy.L / 2;
+    for (int t = HP; t <= std::min(cta_max, round_up(NH, 32)); t += HP)
+      if (t % 32 == 0) add(t);
+  }
+  for (int t : {32, 64, 96, 128, 192, 256, 384, 512, 768, 1024}) {
+    const double sites = static_cast<double>(NH) / t;
+    if (sites >= 2.0 && sites <= 40.0) add(t);
+  }
+  if (c.size() > 8) c.resize(8);
+  return c;
+}
+
+// Pick each system's threads per path by measuring the candidates in the
+// batch's own kernel; leaves the handle planned with the choice.
+int autotune(mp_state* h, const mp_config* cfg) {
+  const int n = static_cast<int>(h->systems.size());
+  h->tp_override.assign(n, 0);
+  int smem_max = 0, cta_max = 0;
+  MP_CUDA(h, sweep_prepare(h->precision, h->variant, h->device, &smem_max, &cta_max));
+  for (int k = 0; k < n; ++k) {
+    // systems of the same lattice kind and size share the choice
+    int same = -1;
+    for (int j = 0; j < k && same < 0; ++j)
+      if (h->systems[j].lattice == h->systems[k].lattice && h->systems[j].L == h->systems[k].L) same = j;
+    if (same >= 0) {
+      h->tp_override[k] = h->tp_override[same];
+      continue;
+    }
+    const std::vector<int> cands = tp_candidates(h, k, cta_max);
+    if (cands.size() < 2) continue;
+    double best = -1.0;
+    int best_t = 0;
+    for (int t : cands) {
+      h->tp_override[k] = t;
+      if (plan(h, cfg) != MP_OK) continue;
+      const double rate = calibrate(h, k);
+      if (rate > best) {
+        best = rate;
+        best_t = t;
+      }
+    }
+    h->tp_override[k] = best_t;
+  }
+  h->err.clear();
+  return plan(h, cfg);
+}
+
 // After the stream has drained: MP_ETIMEOUT if a kernel's bounded wait gave up.
 int check_error_flag(mp_state* h) {
   int flag = 0;
@@ -480,7 +631,7 @@ int mp_create_ex(const mp_config* cfg, mp_handle* out) {
   }
   const int n = static_cast<int>(h->hsys.size());
   h->d_sys = static_cast<DevSystem*>(dev_alloc(h, sizeof(DevSystem) * n));
-  h->d_items = static_cast<WorkItem*>(dev_alloc(h, sizeof(WorkItem) * h->items.size()));
+  h->d_items = static_cast<WorkItem*>(dev_alloc(h, sizeof(WorkItem) * h->total_paths));  // any plan fits
   h->d_queue = static_cast<int*>(dev_alloc(h, 256));
   h->d_rec = static_cast<double*>(dev_alloc(h, sizeof(double) * MP_NREC * h->total_paths));
   h->d_est = static_cast<double*>(dev_alloc(h, sizeof(double) * MP_NEST * n));
@@ -489,24 +640,18 @@ int mp_create_ex(const mp_config* cfg, mp_handle* out) {
     return bail(fail(h, MP_ENOMEM, "device allocation failed"));
   h->d_error = static_cast<int*>(dev_alloc(h, 256));
   if (!h->d_error) return bail(fail(h, MP_ENOMEM, "device allocation failed"));
-  if (h->lattice_groups > 0) {
-    h->lattice_stride = (h->lattice_stride + 255) / 256 * 256;
-    h->d_lattice = dev_alloc(h, static_cast<size_t>(h->grid) * h->lattice_groups * h->lattice_stride);
-    if (!h->d_lattice) return bail(fail(h, MP_ENOMEM, "lattice buffer allocation failed"));
-  }
   if (h->flags & MP_FLAG_KEEP_SPINS) {
     h->d_spins = static_cast<double*>(dev_alloc(h, sizeof(double) * h->total_spins));
     if (!h->d_spins) return bail(fail(h, MP_ENOMEM, "spin buffer allocation failed"));
   }
-  cudaError_t e;
-  if ((e = cudaMemcpyAsync(h->d_sys, h->hsys.data(), sizeof(DevSystem) * n, cudaMemcpyHostToDevice,
-                           h->stream)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(h->d_items, h->items.data(), sizeof(WorkItem) * h->items.size(),
-                           cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(h->d_spin_offset, h->spin_offset.data(), sizeof(int64_t) * n,
-                           cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
-      (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
-    return bail(cuda_fail(h, e, "uploading the work tables"));
+  if ((h->flags & MP_FLAG_AUTOTUNE) && cfg->threads_per_path == 0) {
+    rc = autotune(h, cfg);
+    if (rc != MP_OK) return bail(rc);
+  }
+  rc = ensure_lattice(h);
+  if (rc != MP_OK) return bail(rc);
+  rc = upload_tables(h, h->items);
+  if (rc != MP_OK) return bail(rc);
   *out = h;
   return MP_OK;
 }
@@ -634,6 +779,18 @@ int mp_plan(mp_handle h, int* cta_threads, int* grid, int* smem_bytes, int* n_it
   if (grid) *grid = h->grid;
   if (smem_bytes) *smem_bytes = h->smem;
   if (n_items) *n_items = static_cast<int>(h->items.size());
+  return MP_OK;
+}
+
+int mp_system_plan(mp_handle h, int system, int* threads_per_path, int* paths_per_cta,
+                   int* streamed_from_hbm) {
+  if (!h) return fail(nullptr, MP_EINVAL, "handle is NULL");
+  if (system < 0 || system >= static_cast<int>(h->hsys.size()))
+    return fail(h, MP_EINVAL, "bad system index %d", system);
+  const DevSystem& d = h->hsys[system];
+  if (threads_per_path) *threads_per_path = d.tp;
+  if (paths_per_cta) *paths_per_cta = d.g;
+  if (streamed_from_hbm) *streamed_from_hbm = d.mode == kModeStreamed ? 1 : 0;
   return MP_OK;
 }
 

@@ -116,3 +116,17 @@ def test_fp64_l64_does_not_fit_the_ring():
     with pytest.raises(mp.MPError) as ei:
         mp.Simulation([mp.System(64, 1.44, n_paths=1)], 1, 1, precision=mp.FP64)
     assert ei.value.status == mp.MP_EINVAL
+
+
+def test_autotune_changes_only_the_launch_shape():
+    """MP_FLAG_AUTOTUNE times candidate layouts; the trajectories (and FP64
+    records) do not depend on the layout it keeps."""
+    systems = [mp.System(12, 1.2, n_paths=300), mp.System(8, 1.0, n_paths=500), mp.System(28, 1.4, n_paths=3)]
+    a, pa = gpu_records(systems, 2, 2, seed=4, precision=mp.FP64)
+    b, pb = gpu_records(systems, 2, 2, seed=4, precision=mp.FP64, flags=mp.FLAG_AUTOTUNE)
+    for x, y in zip(a, b):
+        np.testing.assert_allclose(x[:, FIELDS], y[:, FIELDS], rtol=1e-12, atol=1e-14)
+    with mp.Simulation(systems, 1, 1, flags=mp.FLAG_AUTOTUNE) as sim:
+        shapes = [sim.system_plan(k) for k in range(3)]
+    assert shapes[2]["streamed"] and not shapes[0]["streamed"]
+    assert all(s["threads_per_path"] % 32 == 0 for s in shapes)
