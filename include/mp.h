@@ -256,6 +256,46 @@ int mp_timing(mp_handle h, double* sweep_ms, double* reduce_ms);
  * NULL. */
 int mp_plan(mp_handle h, int* cta_threads, int* grid, int* smem_bytes, int* n_items);
 
+/* Resumable runs.  mp_run_sweeps advances every path of every system by
+ * n_sweeps sweeps of its schedule (n_therm thermalisation sweeps, then n_meas
+ * measurement sweeps) from its saved state -- the initial state on the first
+ * call -- and saves the state again (per path: FP64 accumulators, acceptance
+ * count, spins; kept in device memory owned by the handle, allocated on the
+ * first call).  Records and estimates then cover the measurement sweeps done
+ * so far.  Splitting a schedule into several calls gives the same
+ * trajectories as one call (the random numbers depend only on seed, system,
+ * path, sweep and site).  Synchronises; the progress advances only when the
+ * call succeeds.  Independent of mp_run, which always runs the whole schedule.
+ * Errors: MP_EINVAL (n_sweeps < 1), MP_ESTATE (schedule already complete),
+ * MP_ENOMEM, MP_ECANCELED (mp_cancel during the call; state unchanged),
+ * MP_ETIMEOUT, MP_ECUDA. */
+int mp_run_sweeps(mp_handle h, int64_t n_sweeps);
+
+/* Sweeps of the schedule done by mp_run_sweeps so far (or restored). */
+int mp_progress(mp_handle h, int64_t* sweeps_done);
+
+/* Checkpoint of the resumable state.  With buf NULL, *nbytes receives the
+ * size; otherwise buf (caller-owned host memory of *nbytes bytes) receives a
+ * versioned header and the state, and *nbytes the bytes written.  The
+ * checkpoint is valid for a handle of the same configuration (systems,
+ * precision, init mode, seed, schedule, lattice modes).  Synchronises.
+ * Errors: MP_EINVAL (NULL, buffer too small), MP_ESTATE (no mp_run_sweeps yet). */
+int mp_checkpoint(mp_handle h, void* buf, size_t* nbytes);
+
+/* Load a checkpoint written by mp_checkpoint (host memory, read during the
+ * call) into a handle of the same configuration; the next mp_run_sweeps
+ * continues from it.  Errors: MP_EINVAL (not a checkpoint, other
+ * configuration, wrong size), MP_ENOMEM, MP_ECUDA. */
+int mp_restore(mp_handle h, const void* buf, size_t nbytes);
+
+/* Ask the handle's running or next-started kernels to stop: they poll a
+ * host-mapped flag every 16 sweeps, stop at a sweep boundary and write no
+ * record; mp_estimates / mp_paths then return MP_ECANCELED and mp_run_sweeps
+ * leaves the saved state unchanged.  The flag is cleared when the next run
+ * starts.  The one call that may be made from another host thread while a
+ * run is in flight. */
+int mp_cancel(mp_handle h);
+
 /* Launch shape of one system: threads per path, paths per CTA, and whether
  * its lattice is streamed from HBM (1) or held in shared memory (0).  Any
  * output may be NULL.  Errors: MP_EINVAL (bad index). */

@@ -98,7 +98,7 @@ assert ctypes.sizeof(MPEstimates) == NEST * 8
 EXPORTS = [
     "mp_create", "mp_create_ex", "mp_run", "mp_set_seed", "mp_estimates", "mp_paths",
     "mp_device_buffers", "mp_spins", "mp_backward", "mp_timing", "mp_plan", "mp_system_plan",
-    "mp_philox",
+    "mp_run_sweeps", "mp_progress", "mp_checkpoint", "mp_restore", "mp_cancel", "mp_philox",
     "mp_destroy", "mp_last_error", "mp_status_string",
 ]
 
@@ -130,6 +130,11 @@ def load_library(path: str = LIB_PATH):
     lib.mp_timing.argtypes = [H, P(dbl), P(dbl)]
     lib.mp_plan.argtypes = [H] + [P(ctypes.c_int)] * 4
     lib.mp_system_plan.argtypes = [H, ctypes.c_int] + [P(ctypes.c_int)] * 3
+    lib.mp_run_sweeps.argtypes = [H, i64]
+    lib.mp_progress.argtypes = [H, P(i64)]
+    lib.mp_checkpoint.argtypes = [H, ctypes.c_void_p, P(ctypes.c_size_t)]
+    lib.mp_restore.argtypes = [H, ctypes.c_void_p, ctypes.c_size_t]
+    lib.mp_cancel.argtypes = [H]
     lib.mp_philox.argtypes = [ctypes.c_void_p, i64, u64, ctypes.c_void_p, ctypes.c_void_p]
     for name in EXPORTS:
         getattr(lib, name).restype = ctypes.c_int
@@ -319,6 +324,31 @@ class Simulation:
         v = [ctypes.c_int() for _ in range(4)]
         _check(_lib.mp_plan(self._h, *[ctypes.byref(x) for x in v]), self._h)
         return dict(cta_threads=v[0].value, grid=v[1].value, smem_bytes=v[2].value, n_items=v[3].value)
+
+    def run_sweeps(self, n: int):
+        """Advance every path by n sweeps of its schedule from its saved state (synchronous)."""
+        with self.torch.cuda.device(self.device):
+            _check(_lib.mp_run_sweeps(self._h, n), self._h)
+        return self
+
+    def progress(self) -> int:
+        v = ctypes.c_int64()
+        _check(_lib.mp_progress(self._h, ctypes.byref(v)), self._h)
+        return v.value
+
+    def checkpoint(self) -> bytes:
+        n = ctypes.c_size_t(0)
+        _check(_lib.mp_checkpoint(self._h, None, ctypes.byref(n)), self._h)
+        buf = ctypes.create_string_buffer(n.value)
+        _check(_lib.mp_checkpoint(self._h, buf, ctypes.byref(n)), self._h)
+        return buf.raw[: n.value]
+
+    def restore(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(_lib.mp_restore(self._h, buf, len(blob)), self._h)
+
+    def cancel(self):
+        _check(_lib.mp_cancel(self._h), self._h)
 
     def system_plan(self, system: int) -> dict:
         v = [ctypes.c_int() for _ in range(3)]

@@ -58,8 +58,21 @@ struct SweepParams {
   int64_t lattice_stride; // bytes per lattice buffer
   int32_t lattice_groups; // buffers per CTA
   uint32_t test_stall;    // failure injection: streamed paths skip their first bulk copy
-  int* error;             // set to nonzero when a bounded wait gave up
+  int* error;             // kErrTimeout / kErrCanceled when a path stopped early
+  // Resumable runs: sweeps [s_begin, s_end) of the schedule; per-path state
+  // (accumulators, acceptance count, spins) in HBM, loaded and/or saved.
+  int64_t s_begin, s_end;
+  unsigned char* state;
+  const int64_t* state_offset;  // bytes, per system
+  const int64_t* state_stride;  // bytes per path, per system
+  int32_t resume, save;
+  const volatile int* cancel;   // host-mapped cancel flag, or nullptr
 };
+
+constexpr int kErrTimeout = 1;
+constexpr int kErrCanceled = 2;
+constexpr int kStateHeader = 256;  // bytes before a path's spins in its state: acc[24], accepted
+constexpr int kCancelPoll = 16;    // sweeps between polls of the cancel flag
 
 // Byte offsets inside one path's shared-memory slice.
 // [acc: FP64 accumulators][ring: 2 x R sweeps x warps x kRedSlots partials][spins]

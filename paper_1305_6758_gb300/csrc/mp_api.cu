@@ -108,6 +108,15 @@ struct mp_state {
   void* d_lattice = nullptr;       // HBM lattices of streamed paths
   size_t lattice_capacity = 0;     // bytes allocated at d_lattice
   std::vector<int> tp_override;    // per system threads per path (autotuner), 0 = planner
+  // resumable runs (mp_run_sweeps / mp_checkpoint / mp_restore)
+  unsigned char* d_state = nullptr;
+  int64_t state_bytes = 0;
+  std::vector<int64_t> state_offset, state_stride;  // bytes, per system
+  int64_t* d_state_offset = nullptr;
+  int64_t* d_state_stride = nullptr;
+  int64_t sweeps_done = 0;         // progress of the resumable schedule
+  int* h_cancel = nullptr;         // host-mapped cancel flag
+  int* d_cancel = nullptr;
   int64_t lattice_stride = 0;      // bytes per (CTA, group) lattice buffer
   int lattice_groups = 0;          // buffers per CTA
   std::vector<void*> owned;
@@ -189,6 +198,7 @@ void release(mp_state* h) {
     else cudaFree(p);
   }
   h->owned.clear();
+  if (h->h_cancel) cudaFreeHost(h->h_cancel);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -392,7 +402,9 @@ int plan(mp_state* h, const mp_config* cfg) {
   return MP_OK;
 }
 
-int enqueue_run(mp_state* h) {
+// One run of sweeps [s_begin, s_end) of the schedule, then the reduction.
+int enqueue_run(mp_state* h, int64_t s_begin, int64_t s_end, bool resume, bool save,
+                bool capturing = false) {
   SweepParams p{};
   p.systems = h->d_sys;
   p.items = h->d_items;
@@ -408,15 +420,22 @@ int enqueue_run(mp_state* h) {
   p.lattice_groups = h->lattice_groups;
   p.error = h->d_error;
   p.test_stall = (h->flags & MP_FLAG_TEST_STALL) ? 1u : 0u;
+  p.s_begin = s_begin;
+  p.s_end = s_end;
+  p.state = save || resume ? h->d_state : nullptr;
+  p.state_offset = h->d_state_offset;
+  p.state_stride = h->d_state_stride;
+  p.resume = resume ? 1 : 0;
+  p.save = save ? 1 : 0;
+  p.cancel = h->d_cancel;
   p.n_therm = h->n_therm;
   p.n_meas = h->n_meas;
   ReduceParams r{};
   r.systems = h->d_sys;
   r.records = h->d_rec;
   r.est = h->d_est;
-  r.n_therm = h->n_therm;
-  r.n_meas = h->n_meas;
-  const bool capturing = h->flags & MP_FLAG_GRAPH;
+  r.n_therm = std::min(s_end, h->n_therm);
+  r.n_meas = std::max<int64_t>(0, s_end - h->n_therm);
   const unsigned evflag = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   MP_CUDA(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int), h->stream));
   MP_CUDA(h, cudaMemsetAsync(h->d_error, 0, sizeof(int), h->stream));
@@ -480,6 +499,8 @@ double calibrate(mp_state* h, int k) {
   p.init_mode = h->init_mode;
   p.n_therm = sweeps - 1;
   p.n_meas = 1;
+  p.s_begin = 0;
+  p.s_end = sweeps;
   p.key = philox_round_keys(h->seed);
   p.lattice = h->d_lattice;
   p.lattice_stride = h->lattice_stride;
@@ -567,6 +588,7 @@ int autotune(mp_state* h, const mp_config* cfg) {
 int check_error_flag(mp_state* h) {
   int flag = 0;
   MP_CUDA(h, cudaMemcpy(&flag, h->d_error, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag == kErrCanceled) return fail(h, MP_ECANCELED, "the run was canceled; results invalid");
   if (flag) return fail(h, MP_ETIMEOUT, "a bulk copy did not complete in time; results invalid");
   return MP_OK;
 }
@@ -629,6 +651,13 @@ int mp_create_ex(const mp_config* cfg, mp_handle* out) {
     cudaError_t ce = cudaEventCreate(&e);
     if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "cudaEventCreate"));
   }
+  {  // the cancel flag: host memory the kernels can read while they run
+    cudaError_t ce = cudaHostAlloc(reinterpret_cast<void**>(&h->h_cancel), sizeof(int), cudaHostAllocMapped);
+    if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "cudaHostAlloc"));
+    *h->h_cancel = 0;
+    ce = cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->d_cancel), h->h_cancel, 0);
+    if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "cudaHostGetDevicePointer"));
+  }
   const int n = static_cast<int>(h->hsys.size());
   h->d_sys = static_cast<DevSystem*>(dev_alloc(h, sizeof(DevSystem) * n));
   h->d_items = static_cast<WorkItem*>(dev_alloc(h, sizeof(WorkItem) * h->total_paths));  // any plan fits
@@ -660,7 +689,8 @@ int mp_run(mp_handle h) {
   if (!h) return fail(nullptr, MP_EINVAL, "handle is NULL");
   DeviceGuard dg(h->device);
   if (!(h->flags & MP_FLAG_GRAPH)) {
-    int rc = enqueue_run(h);
+    *h->h_cancel = 0;
+    int rc = enqueue_run(h, 0, h->n_therm + h->n_meas, false, false);
     if (rc != MP_OK) return rc;
     h->ran = true;
     return MP_OK;
@@ -671,7 +701,7 @@ int mp_run(mp_handle h) {
       h->gexec = nullptr;
     }
     MP_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    int rc = enqueue_run(h);
+    int rc = enqueue_run(h, 0, h->n_therm + h->n_meas, false, false, true);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
     if (rc != MP_OK) {
@@ -684,6 +714,7 @@ int mp_run(mp_handle h) {
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
     h->graph_dirty = false;
   }
+  *h->h_cancel = 0;
   MP_CUDA(h, cudaGraphLaunch(h->gexec, h->stream));
   h->ran = true;
   return MP_OK;
@@ -779,6 +810,159 @@ int mp_plan(mp_handle h, int* cta_threads, int* grid, int* smem_bytes, int* n_it
   if (grid) *grid = h->grid;
   if (smem_bytes) *smem_bytes = h->smem;
   if (n_items) *n_items = static_cast<int>(h->items.size());
+  return MP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Per-path resumable state: kStateHeader bytes of accumulators, then the spins
+// in the kernel's own layout (colour-split SoA for shared-memory paths, the
+// padded half-plane layout for streamed ones).
+int ensure_state(mp_state* h) {
+  if (h->d_state) return MP_OK;
+  const int n = static_cast<int>(h->hsys.size());
+  const int real = h->precision == MP_FP64 ? 8 : 4;
+  h->state_offset.assign(n, 0);
+  h->state_stride.assign(n, 0);
+  int64_t off = 0;
+  for (int k = 0; k < n; ++k) {
+    const DevSystem& d = h->hsys[k];
+    const int64_t spins = d.mode == kModeStreamed
+                              ? static_cast<int64_t>(2) * d.L * half_plane_bytes(d.L, real)
+                              : static_cast<int64_t>(6) * d.NH * real;
+    h->state_stride[k] = (kStateHeader + spins + 255) / 256 * 256;
+    h->state_offset[k] = off;
+    off += h->state_stride[k] * d.n_paths;
+  }
+  h->state_bytes = off;
+  h->d_state = static_cast<unsigned char*>(dev_alloc(h, static_cast<size_t>(off)));
+  h->d_state_offset = static_cast<int64_t*>(dev_alloc(h, sizeof(int64_t) * n));
+  h->d_state_stride = static_cast<int64_t*>(dev_alloc(h, sizeof(int64_t) * n));
+  if (!h->d_state || !h->d_state_offset || !h->d_state_stride)
+    return fail(h, MP_ENOMEM, "state allocation failed (%lld bytes)", static_cast<long long>(off));
+  MP_CUDA(h, cudaMemcpyAsync(h->d_state_offset, h->state_offset.data(), sizeof(int64_t) * n,
+                             cudaMemcpyHostToDevice, h->stream));
+  MP_CUDA(h, cudaMemcpyAsync(h->d_state_stride, h->state_stride.data(), sizeof(int64_t) * n,
+                             cudaMemcpyHostToDevice, h->stream));
+  MP_CUDA(h, cudaStreamSynchronize(h->stream));
+  return MP_OK;
+}
+
+struct CheckpointHeader {
+  char magic[8];
+  uint64_t version;
+  uint64_t config_hash;
+  int64_t sweeps_done;
+  int64_t state_bytes;
+  int64_t reserved[3];
+};
+
+// FNV-1a over everything the state depends on: systems, precision, seed,
+// schedule, init mode and each system's lattice mode.
+uint64_t config_hash(const mp_state* h) {
+  uint64_t x = 1469598103934665603ull;
+  auto mix = [&](const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) x = (x ^ b[i]) * 1099511628211ull;
+  };
+  for (const mp_system& s : h->systems) {
+    mix(&s.lattice, sizeof(s.lattice));
+    mix(&s.L, sizeof(s.L));
+    mix(&s.T, sizeof(s.T));
+    mix(&s.J, sizeof(s.J));
+    mix(&s.h, sizeof(s.h));
+    mix(&s.n_paths, sizeof(s.n_paths));
+  }
+  for (const DevSystem& d : h->hsys) mix(&d.mode, sizeof(d.mode));
+  mix(&h->precision, sizeof(h->precision));
+  mix(&h->init_mode, sizeof(h->init_mode));
+  mix(&h->seed, sizeof(h->seed));
+  mix(&h->n_therm, sizeof(h->n_therm));
+  mix(&h->n_meas, sizeof(h->n_meas));
+  return x;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mp_run_sweeps(mp_handle h, int64_t n_sweeps) {
+  if (!h) return fail(nullptr, MP_EINVAL, "handle is NULL");
+  const int64_t total = h->n_therm + h->n_meas;
+  if (n_sweeps < 1) return fail(h, MP_EINVAL, "n_sweeps must be >= 1");
+  if (h->sweeps_done >= total) return fail(h, MP_ESTATE, "the schedule of %lld sweeps is complete",
+                                           static_cast<long long>(total));
+  DeviceGuard dg(h->device);
+  int rc = ensure_state(h);
+  if (rc != MP_OK) return rc;
+  const int64_t s_end = std::min(total, h->sweeps_done + n_sweeps);
+  *h->h_cancel = 0;
+  rc = enqueue_run(h, h->sweeps_done, s_end, h->sweeps_done > 0, true);
+  if (rc != MP_OK) return rc;
+  MP_CUDA(h, cudaStreamSynchronize(h->stream));
+  rc = check_error_flag(h);
+  if (rc != MP_OK) return rc;  // canceled or timed out: the saved state is unchanged
+  h->sweeps_done = s_end;
+  if (s_end > h->n_therm) h->ran = true;
+  return MP_OK;
+}
+
+int mp_progress(mp_handle h, int64_t* sweeps_done) {
+  if (!h || !sweeps_done) return fail(h, MP_EINVAL, "NULL argument");
+  *sweeps_done = h->sweeps_done;
+  return MP_OK;
+}
+
+int mp_checkpoint(mp_handle h, void* buf, size_t* nbytes) {
+  if (!h || !nbytes) return fail(h, MP_EINVAL, "NULL argument");
+  if (h->sweeps_done == 0 || !h->d_state) return fail(h, MP_ESTATE, "nothing to checkpoint (no mp_run_sweeps yet)");
+  const size_t need = sizeof(CheckpointHeader) + static_cast<size_t>(h->state_bytes);
+  if (!buf) {
+    *nbytes = need;
+    return MP_OK;
+  }
+  if (*nbytes < need) return fail(h, MP_EINVAL, "buffer of %zu bytes, need %zu", *nbytes, need);
+  DeviceGuard dg(h->device);
+  CheckpointHeader hd{};
+  std::memcpy(hd.magic, "MPCKPT01", 8);
+  hd.version = 1;
+  hd.config_hash = config_hash(h);
+  hd.sweeps_done = h->sweeps_done;
+  hd.state_bytes = h->state_bytes;
+  std::memcpy(buf, &hd, sizeof(hd));
+  MP_CUDA(h, cudaMemcpyAsync(static_cast<unsigned char*>(buf) + sizeof(hd), h->d_state,
+                             static_cast<size_t>(h->state_bytes), cudaMemcpyDeviceToHost, h->stream));
+  MP_CUDA(h, cudaStreamSynchronize(h->stream));
+  *nbytes = need;
+  return MP_OK;
+}
+
+int mp_restore(mp_handle h, const void* buf, size_t nbytes) {
+  if (!h || !buf) return fail(h, MP_EINVAL, "NULL argument");
+  if (nbytes < sizeof(CheckpointHeader)) return fail(h, MP_EINVAL, "checkpoint too short");
+  CheckpointHeader hd;
+  std::memcpy(&hd, buf, sizeof(hd));
+  if (std::memcmp(hd.magic, "MPCKPT01", 8) != 0 || hd.version != 1)
+    return fail(h, MP_EINVAL, "not a checkpoint of this library");
+  if (hd.config_hash != config_hash(h))
+    return fail(h, MP_EINVAL, "checkpoint of a different configuration");
+  DeviceGuard dg(h->device);
+  int rc = ensure_state(h);
+  if (rc != MP_OK) return rc;
+  if (hd.state_bytes != h->state_bytes || nbytes < sizeof(hd) + static_cast<size_t>(hd.state_bytes))
+    return fail(h, MP_EINVAL, "checkpoint size does not match");
+  MP_CUDA(h, cudaMemcpyAsync(h->d_state, static_cast<const unsigned char*>(buf) + sizeof(hd),
+                             static_cast<size_t>(hd.state_bytes), cudaMemcpyHostToDevice, h->stream));
+  MP_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->sweeps_done = hd.sweeps_done;
+  return MP_OK;
+}
+
+int mp_cancel(mp_handle h) {
+  if (!h) return fail(nullptr, MP_EINVAL, "handle is NULL");
+  *reinterpret_cast<volatile int*>(h->h_cancel) = 1;
   return MP_OK;
 }
 

@@ -159,6 +159,8 @@ extern "C" int mp_run_noalloc(const mp_system* systems, int n_systems, int preci
   p.init_mode = MP_INIT_SPHERE;
   p.n_therm = n_therm;
   p.n_meas = n_meas;
+  p.s_begin = 0;
+  p.s_end = n_therm + n_meas;
   p.key = mpk::philox_round_keys(seed);
   mpk::ReduceParams r{};
   r.systems = d->systems;

@@ -344,6 +344,7 @@ struct Meter {
   int R, nwarps, lane, warp, tid;
   double invN;
   Real J, hf;
+  int64_t j_first;  // first measurement sweep of this call (earlier ones are already flushed)
 
   __device__ Real* slot(int64_t j) const {
     return red + ((((j / R) & 1) * R + (j % R)) * nwarps) * kRedSlots;
@@ -417,12 +418,19 @@ struct Meter {
   }
   // At measurement sweep j, after its first barrier: flush the previous half.
   __device__ void maybe_flush(int64_t j) const {
-    if (j > 0 && (j % R) == 0) flush(j - R, R);
+    if (j > j_first && (j % R) == 0) {
+      const int64_t j0 = j - R > j_first ? j - R : j_first;
+      flush(j0, static_cast<int>(j - j0));
+    }
   }
-  // After the last sweep's final barrier: flush the rest, keep the final state.
+  // After the call's last sweep and its barrier: flush the rest of the
+  // measurement sweeps j_first .. n_meas-1 and keep the final state.
   __device__ void finish(int64_t n_meas) const {
     const int64_t last = n_meas - 1;
-    flush(last - last % R, static_cast<int>(last % R) + 1);
+    if (last < j_first) return;  // no measurement sweep in this call
+    int64_t j0 = last - last % R;
+    if (j0 < j_first) j0 = j_first;
+    flush(j0, static_cast<int>(last - j0) + 1);
     if (tid == 0) {  // the final state: the paper's per-path output
       Real e, ex, ey, ez;
       observe(slot(last), e, ex, ey, ez);
@@ -435,7 +443,8 @@ struct Meter {
   // Reduce the acceptance count and the worst | |S| - 1 | over the group and
   // write the path's record (the ring area is reused; call after a barrier).
   __device__ void write_record(double* rec, int accepted, double worst, int64_t nsweeps,
-                               int64_t n_meas, int N, int tp, int bar) const {
+                               int64_t n_meas, int N, int tp, int bar, double accepted_before,
+                               double* save_accepted) const {
     double nacc = static_cast<double>(accepted);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -449,12 +458,13 @@ struct Meter {
     }
     group_sync(tp, bar);
     if (tid == 0) {
-      double tot = 0.0, wmax = 0.0;
+      double tot = accepted_before, wmax = 0.0;
       for (int w = 0; w < nwarps; ++w) {
         tot += fin[2 * w + 0];
         wmax = fmax(wmax, fin[2 * w + 1]);
       }
-      const double inv = 1.0 / static_cast<double>(n_meas);
+      if (save_accepted) *save_accepted = tot;
+      const double inv = n_meas > 0 ? 1.0 / static_cast<double>(n_meas) : NAN;
       for (int k = MP_R_E; k <= MP_R_MMZ; ++k) rec[k] = acc[k] * inv;
       for (int k = MP_R_FMX; k <= MP_R_FE; ++k) rec[k] = acc[k];
       rec[MP_R_ACC] = tot / (static_cast<double>(nsweeps) * static_cast<double>(N));
@@ -482,6 +492,22 @@ __device__ __forceinline__ void initial_spin(uint32_t i, uint32_t c2, uint32_t c
   }
 }
 
+// --------------------------------------------------------- resumable state --
+// A path's state in HBM (resumable runs): [acc: 24 doubles][accepted: double]
+// padded to kStateHeader bytes, then its spins.
+__device__ __forceinline__ unsigned char* path_state(const SweepParams& P, int sys_idx, int64_t path) {
+  return P.state ? P.state + P.state_offset[sys_idx] + path * P.state_stride[sys_idx] : nullptr;
+}
+
+// Poll of the host's cancel flag by one thread of the group, every kCancelPoll
+// sweeps of a call; the group reads the verdict after its next barrier.
+__device__ __forceinline__ void poll_cancel(const SweepParams& P, int64_t s, int tid, int* flag) {
+  if (tid == 0 && P.cancel != nullptr && ((s - P.s_begin) % kCancelPoll) == 0 && *P.cancel != 0) {
+    *flag = 1;
+    atomicExch(P.error, kErrCanceled);
+  }
+}
+
 // ------------------------------------------------------------- one path --
 template <typename Real, class Geom>
 __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, int sys_idx,
@@ -496,37 +522,55 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
   const Real J = static_cast<Real>(sy.J), hf = static_cast<Real>(sy.h);
   const Real bp = A::beta_param(sy.beta);
   const bool columns = Geom::kColumns && (tp % Geom::HP) == 0;
+  const int64_t j_first = P.s_begin > P.n_therm ? P.s_begin - P.n_therm : 0;
   const Meter<Real> meter{reinterpret_cast<double*>(slice + slice_acc_offset()),
                           reinterpret_cast<Real*>(slice + slice_red_offset()),
                           sy.ring, tp >> 5, tid & 31, tid >> 5, tid,
-                          1.0 / static_cast<double>(sy.N), J, hf};
+                          1.0 / static_cast<double>(sy.N), J, hf, j_first};
+  unsigned char* st = path_state(P, sys_idx, path);
+  Real* st_spins = st ? reinterpret_cast<Real*>(st + kStateHeader) : nullptr;
+  __shared__ int cancel_flag[16];
+  const int gidx = bar - 1;
 
-  for (int c = 0; c < 2; ++c) {
-    Real* own = sp + c * 3 * S;
-    const int cnt = geo.count(c);
-    for (int hh = tid; hh < cnt; hh += tp) {
-      int nb[Geom::NNB];
-      int nn;
-      const int i = geo.site(hh, c, nb, nn);
-      Real x, y, z;
-      initial_spin<Real>(static_cast<uint32_t>(i), c2, c3i, P, x, y, z);
-      own[hh] = x;
-      own[S + hh] = y;
-      own[2 * S + hh] = z;
+  if (P.resume && st) {  // continue from the saved state
+    for (int k = tid; k < 6 * S; k += tp) sp[k] = st_spins[k];
+    if (tid < kAccDoubles) meter.acc[tid] = reinterpret_cast<const double*>(st)[tid];
+  } else {
+    for (int c = 0; c < 2; ++c) {
+      Real* own = sp + c * 3 * S;
+      const int cnt = geo.count(c);
+      for (int hh = tid; hh < cnt; hh += tp) {
+        int nb[Geom::NNB];
+        int nn;
+        const int i = geo.site(hh, c, nb, nn);
+        Real x, y, z;
+        initial_spin<Real>(static_cast<uint32_t>(i), c2, c3i, P, x, y, z);
+        own[hh] = x;
+        own[S + hh] = y;
+        own[2 * S + hh] = z;
+      }
     }
+    if (tid < kAccDoubles) meter.acc[tid] = 0.0;
   }
-  if (tid < kAccDoubles) meter.acc[tid] = 0.0;
+  const double accepted_before =
+      (P.resume && st) ? reinterpret_cast<const double*>(st)[kAccDoubles] : 0.0;
+  if (tid == 0) cancel_flag[gidx] = 0;
   group_sync(tp, bar);
 
   int accepted = 0;
-  const int64_t nsweeps = P.n_therm + P.n_meas;
-  for (int64_t s = 0; s < nsweeps; ++s) {
+  bool canceled = false;
+  for (int64_t s = P.s_begin; s < P.s_end; ++s) {
     const uint32_t sw = static_cast<uint32_t>(s);
     Partials<Real> part{Real(0), Real(0), Real(0), Real(0)};
+    poll_cancel(P, s, tid, &cancel_flag[gidx]);
     if (s < P.n_therm) {
       half_sweep<Real, Geom, false, false>(geo, 0, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf,
                                            bp, accepted, part);
       group_sync(tp, bar);
+      if (cancel_flag[gidx]) {
+        canceled = true;
+        break;
+      }
       half_sweep<Real, Geom, false, false>(geo, 1, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf,
                                            bp, accepted, part);
       group_sync(tp, bar);
@@ -538,13 +582,22 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
     half_sweep<Real, Geom, true, false>(geo, 0, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf, bp,
                                         accepted, part);
     group_sync(tp, bar);
+    if (cancel_flag[gidx]) {
+      canceled = true;
+      break;
+    }
     meter.maybe_flush(j);
     half_sweep<Real, Geom, true, true>(geo, 1, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf, bp,
                                        accepted, part);
     meter.record(j, part);
     group_sync(tp, bar);
   }
-  meter.finish(P.n_meas);
+  if (canceled) {  // the call is discarded: no record, no saved state
+    group_sync(tp, bar);
+    return;
+  }
+  const int64_t n_meas_done = P.s_end > P.n_therm ? P.s_end - P.n_therm : 0;
+  meter.finish(n_meas_done);
   group_sync(tp, bar);
 
   Real worst = Real(0);
@@ -555,8 +608,13 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
       worst = fmax(worst, fabs(sqrt(x * x + y * y + z * z) - Real(1)));
     }
   }
+  if (P.save && st) {
+    for (int k = tid; k < 6 * S; k += tp) st_spins[k] = sp[k];
+    if (tid < kAccDoubles) reinterpret_cast<double*>(st)[tid] = meter.acc[tid];
+  }
   meter.write_record(P.records + (sy.rec_offset + path) * MP_NREC, accepted,
-                     static_cast<double>(worst), nsweeps, P.n_meas, sy.N, tp, bar);
+                     static_cast<double>(worst), P.s_end, n_meas_done, sy.N, tp, bar,
+                     accepted_before, (P.save && st) ? reinterpret_cast<double*>(st) + kAccDoubles : nullptr);
   if (P.spins != nullptr) {
     double* out = P.spins + P.spin_offset[sys_idx] + path * 3 * static_cast<int64_t>(sy.N);
     for (int c = 0; c < 2; ++c) {
@@ -678,7 +736,7 @@ struct StreamLayout {
 template <typename Real>
 __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path,
                                   const SweepParams& P, unsigned char* slice, int tid, int tp,
-                                  int bar, Real* lat) {
+                                  int bar, Real* lat_cta) {
   using A = Arith<Real>;
   const int L = sy.L, HL = L / 2, HP = L * L / 2;
   const int hps = StreamLayout<Real>::hps(L);
@@ -692,6 +750,10 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
   auto c1buf = [&](int q) { return buf + (4 + (q + 1) % 5) * hps; };
   auto c0bar = [&](int q) { return mbar + (q & 3); };
   auto c1bar = [&](int q) { return mbar + 4 + (q + 1) % 5; };
+  // a resumable run keeps the path's lattice in its state; otherwise the
+  // group's own HBM buffer holds it for the run
+  unsigned char* st = path_state(P, sys_idx, path);
+  Real* lat = st ? reinterpret_cast<Real*>(st + kStateHeader) : lat_cta;
   auto plane = [&](int z, int c) { return lat + (static_cast<int64_t>(z) * 2 + c) * hps; };
   auto wrap = [&](int q) { return ((q % L) + L) % L; };
   const uint32_t c2 = static_cast<uint32_t>(path);
@@ -699,17 +761,20 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
   const uint32_t c3i = kTagInit | (static_cast<uint32_t>(sys_idx) << 8);
   const Real J = static_cast<Real>(sy.J), hf = static_cast<Real>(sy.h);
   const Real bp = A::beta_param(sy.beta);
+  const int64_t j_first = P.s_begin > P.n_therm ? P.s_begin - P.n_therm : 0;
   const Meter<Real> meter{reinterpret_cast<double*>(slice + slice_acc_offset()),
                           reinterpret_cast<Real*>(slice + slice_red_offset()),
                           sy.ring, tp >> 5, tid & 31, tid >> 5, tid,
-                          1.0 / static_cast<double>(sy.N), J, hf};
-  __shared__ int abort_flag[16];  // per thread group: a bounded wait gave up
+                          1.0 / static_cast<double>(sy.N), J, hf, j_first};
+  __shared__ int abort_flag[16];  // per thread group: a bounded wait gave up, or canceled
   const int gidx = bar - 1;
   const bool producer = tid == 0;
+  const bool resume = P.resume && st;
+  const double accepted_before = resume ? reinterpret_cast<const double*>(st)[kAccDoubles] : 0.0;
 
   // Initial state straight into HBM (generic stores), visible to the bulk copies.
   const int N = sy.N;
-  for (int i = tid; i < N; i += tp) {
+  for (int i = resume ? N : tid; i < N; i += tp) {
     const int x = i % L, y = (i / L) % L, z = i / (L * L);
     const int c = (x + y + z) & 1;
     Real sx, sy_, sz;
@@ -721,7 +786,7 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
     hpl[2 * HP + hp] = sz;
   }
   fence_async_global();
-  if (tid < kAccDoubles) meter.acc[tid] = 0.0;
+  if (tid < kAccDoubles) meter.acc[tid] = resume ? reinterpret_cast<const double*>(st)[tid] : 0.0;
   if (tid == 0) abort_flag[gidx] = 0;
   if (producer) {
     for (int k = 0; k < kSlots; ++k) {
@@ -745,20 +810,20 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
   // j of a ring of n slots takes the shifted step indices j, j + n, ... <= L+1
   auto per_sweep = [&](int j, int n) { return (L + 1 - j) / n + 1; };
   int accepted = 0;
-  const int64_t nsweeps = P.n_therm + P.n_meas;
   bool ok = true;
 
-  for (int64_t s = 0; s < nsweeps && ok; ++s) {
+  for (int64_t s = P.s_begin; s < P.s_end && ok; ++s) {
     const uint32_t sw = static_cast<uint32_t>(s);
     const bool meas = s >= P.n_therm;
     const int64_t j = s - P.n_therm;
     Partials<Real> part{Real(0), Real(0), Real(0), Real(0)};
+    const int64_t sc = s - P.s_begin;  // sweeps since the mbarriers were initialised
     auto parity0 = [&](int q) {
-      return static_cast<uint32_t>((s * per_sweep(q & 3, 4) + q / 4) & 1);
+      return static_cast<uint32_t>((sc * per_sweep(q & 3, 4) + q / 4) & 1);
     };
     auto parity1 = [&](int q) {
       const int qq = q + 1;
-      return static_cast<uint32_t>((s * per_sweep(qq % 5, 5) + qq / 5) & 1);
+      return static_cast<uint32_t>((sc * per_sweep(qq % 5, 5) + qq / 5) & 1);
     };
     // Buffers first used at step q: colour-0 index q, colour-1 index q+1 (at
     // q = 0 also colour-1 indices -1 and 0).  Only the producer waits on their
@@ -772,9 +837,12 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
       if (q < L) w = w && mbar_wait(c1bar(q + 1), parity1(q + 1), P.error);
       if (!w) abort_flag[gidx] = 1;
     };
-    if (producer) {
+    int cancel = 0;
+    poll_cancel(P, s, tid, &cancel);
+    if (producer && cancel) abort_flag[gidx] = 1;  // stop before any copy of this sweep
+    if (producer && !cancel) {
       tma_wait_all();  // the previous sweep's write-backs are complete
-      if (!(P.test_stall && s == 0)) load(c0buf(0), plane(0, 0), 0);
+      if (!(P.test_stall && s == P.s_begin)) load(c0buf(0), plane(0, 0), 0);
       load(c0buf(1), plane(1 % L, 0), 1);
       for (int q1 = -1; q1 <= 2; ++q1) load(c1buf(q1), plane(wrap(q1), 1), 4 + (q1 + 1) % 5);
       wait_step(0);
@@ -868,7 +936,8 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
   }
   group_sync(tp, bar);
   if (!ok) return;  // the error flag is set; the path's record is not written
-  meter.finish(P.n_meas);
+  const int64_t n_meas_done = P.s_end > P.n_therm ? P.s_end - P.n_therm : 0;
+  meter.finish(n_meas_done);
   group_sync(tp, bar);
 
   Real worst = Real(0);  // in the working precision: FP64 runs at 1/64 rate on this GPU
@@ -885,8 +954,10 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
       out[3 * i + 2] = c;
     }
   }
+  if (P.save && st && tid < kAccDoubles) reinterpret_cast<double*>(st)[tid] = meter.acc[tid];
   meter.write_record(P.records + (sy.rec_offset + path) * MP_NREC, accepted,
-                     static_cast<double>(worst), nsweeps, P.n_meas, N, tp, bar);
+                     static_cast<double>(worst), P.s_end, n_meas_done, N, tp, bar, accepted_before,
+                     (P.save && st) ? reinterpret_cast<double*>(st) + kAccDoubles : nullptr);
   group_sync(tp, bar);  // the slice and the HBM buffer are reused by the next item
 }
 
