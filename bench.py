@@ -14,6 +14,10 @@ unit-spin lattices drawn from Philox inside the kernels).  Workloads:
   batched  uneven sizes in one persistent launch: L in {8,12,16,20,24,32} with
            8192/4096/2048/1024/512/256 paths, T=1.44, 1000 + 1000 sweeps, FP32.
   plain    simple cubic L=4, T=1.5, 256 paths, 1000 + 1000 sweeps, FP64.
+  ising    Appendix A: square-lattice Ising L=60, T in {1.0, 2.0, 2.269, 3.0},
+           10^4 paths each, 10^4 + 2x10^4 sweeps (3x10^4 as in the appendix).
+  random   the paper's literal order (N attempts at random sites per sweep):
+           simple cubic L=10, T=1.0, 10^4 paths, 500 + 500 sweeps, FP32.
 
 value: spin-update attempts/s over all ranks (sites x paths x sweeps /
 device time of the timed steps, max over ranks).  Each rank runs its own full
@@ -66,7 +70,31 @@ WORKLOADS = {
         cpu_paths=256, ref_paths=256, fp64_paths=0,
         text=("plain method, FP64: simple cubic L=4, J=1, h=0, T=1.5, 256 paths, 1000+1000 "
               "checkerboard sweeps")),
+    "ising": dict(
+        systems=[(60, T, 10000, "ising") for T in (1.0, 2.0, 2.269, 3.0)], n_therm=10000,
+        n_meas=20000, precision="fp32", bound="alu_ising", cpu_paths=1, ref_paths=1, fp64_paths=0,
+        text=("square-lattice Ising L=60 periodic (Appendix A), J=1, h=0, T in {1.0,2.0,2.269,3.0}, "
+              "10^4 paths each, 10^4+2x10^4 checkerboard sweeps, byte spins in shared memory, "
+              "integer acceptance thresholds, FP64 accumulators")),
+    "random": dict(
+        systems=[(10, 1.0, 10000)], n_therm=500, n_meas=500, precision="fp32", bound="alu",
+        cpu_paths=2, ref_paths=2, fp64_paths=0, flags="random_site", order="random",
+        text=("the paper's literal order, N attempts at random sites per sweep: simple cubic L=10, "
+              "J=1, h=0, T=1.0, 10^4 paths, 500+500 sweeps, FP32, one thread per path, lattices "
+              "in HBM")),
 }
+
+LATTICES = {"sc": 0, "chain": 1, "ising": 2}
+
+
+def sites(entry) -> int:
+    """Sites of a workload system (L, T, paths[, lattice])."""
+    L, kind = entry[0], (entry[3] if len(entry) > 3 else "sc")
+    return L ** 2 if kind == "ising" else (L if kind == "chain" else L ** 3)
+
+
+def lattice_of(entry) -> int:
+    return LATTICES[entry[3] if len(entry) > 3 else "sc"]
 
 # Algorithmic lane operations of one Metropolis attempt (instruction-bound
 # kernels): Philox4x32-10 40 (10 rounds x 2 wide multiplies + 2 three-input
@@ -75,6 +103,10 @@ WORKLOADS = {
 # accept 5 (scale, exp, two compares, select), store 3, measurement 2 (about
 # 4.5 on the half of the sweeps that measure).
 OPS_PER_ATTEMPT = 109
+# Ising (Appendix A kernel): a quarter Philox call 10, own spin and four
+# neighbour byte loads 5, three adds 3, threshold index and load 3, compare 1,
+# flip store and count 2 (on accept; counted once), measurement 1.
+OPS_PER_ATTEMPT_ISING = 25
 # Algorithmic HBM bytes of one attempt when the lattice streams from HBM:
 # each spin is read once and written once per sweep, 3 components x 4 bytes.
 BYTES_PER_ATTEMPT_FP32 = 24
@@ -89,7 +121,7 @@ def load_peaks():
 
 
 def attempts_of(systems, sweeps, paths_override=None):
-    return sum(Ls ** 3 * (paths_override or P) * sweeps for Ls, _, P in systems)
+    return sum(sites(e) * (paths_override or e[2]) * sweeps for e in systems)
 
 
 def oracle_sample(w, paths_per_system: int, threads: int | None = None):
@@ -97,12 +129,13 @@ def oracle_sample(w, paths_per_system: int, threads: int | None = None):
     import oracle
 
     oracle.build()
-    systems = [oracle.System(Ls, T, n_paths=P, path_begin=0, path_count=min(paths_per_system, P))
-               for Ls, T, P in w["systems"]]
+    systems = [oracle.System(e[0], e[1], n_paths=e[2], path_begin=0, path_count=min(paths_per_system, e[2]),
+                             lattice=lattice_of(e)) for e in w["systems"]]
+    order = oracle.ORDER_RANDOM if w.get("order") == "random" else oracle.ORDER_CHECKER
     t0 = time.perf_counter()
-    oracle.run(systems, w["n_therm"], w["n_meas"], seed=1, threads=threads)
+    oracle.run(systems, w["n_therm"], w["n_meas"], seed=1, threads=threads, order_mode=order)
     dt = time.perf_counter() - t0
-    att = sum(s.L ** 3 * s.path_count * (w["n_therm"] + w["n_meas"]) for s in systems)
+    att = sum(s.N * s.path_count * (w["n_therm"] + w["n_meas"]) for s in systems)
     return att, dt
 
 
@@ -251,9 +284,9 @@ def main():
     n_therm, n_meas = w["n_therm"], w["n_meas"]
     sweeps = n_therm + n_meas
     precision = mp.FP64 if w["precision"] == "fp64" else mp.FP32
-    systems = [mp.System(Ls, T, n_paths=P) for Ls, T, P in w["systems"]]
+    systems = [mp.System(e[0], e[1], n_paths=e[2], lattice=lattice_of(e)) for e in w["systems"]]
     n_sys = len(systems)
-    tune = mp.FLAG_AUTOTUNE
+    tune = mp.FLAG_AUTOTUNE | (mp.FLAG_RANDOM_SITE if w.get("flags") == "random_site" else 0)
     sim = mp.Simulation(systems, n_therm, n_meas, seed=seed, precision=precision, device=dev, flags=tune)
     stream = sim.stream
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
@@ -286,7 +319,7 @@ def main():
 
     total_ms = max_over_ranks(sum(step_ms), dist, dev)
     attempts_rank = attempts_of(w["systems"], sweeps)
-    paths_rank = sum(P for _, _, P in w["systems"])
+    paths_rank = sum(e[2] for e in w["systems"])
     value = job_throughput(attempts_rank, world, args.steps, total_ms)
     paths_per_s = job_throughput(paths_rank, world, args.steps, total_ms)
     ests = [sim.estimates(k) for k in range(n_sys)]
@@ -305,8 +338,8 @@ def main():
             plan = s2.plan()
         e2e_s.append(time.perf_counter() - t0)
     # the caller's system table, then the library's DevSystem (88 B), WorkItem
-    # (16 B) and spin-offset (8 B) tables
-    h2d_total = (ctypes.sizeof(mp.MPSystem) + 88 + 8) * n_sys + 16 * plan["n_items"]
+    # (16 B), spin-offset (8 B) and Ising-threshold (80 B) tables
+    h2d_total = (ctypes.sizeof(mp.MPSystem) + 88 + 8 + 80) * n_sys + 16 * plan["n_items"]
     d2h_total = ctypes.sizeof(mp.MPEstimates) * n_sys
     e2e_value = attempts_rank * world / (sum(e2e_s) / len(e2e_s))
 
@@ -323,16 +356,20 @@ def main():
     else:
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
         peak = n_sm * 128 * sm_max * 1e6 / 1e12  # lane-ops/s in units of 1e12
-        achieved = OPS_PER_ATTEMPT * kernel_rate / 1e12
+        ops = OPS_PER_ATTEMPT_ISING if w["bound"] == "alu_ising" else OPS_PER_ATTEMPT
+        achieved = ops * kernel_rate / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": None, "ops_per_attempt": OPS_PER_ATTEMPT,
+                "traffic": None, "ops_per_attempt": ops,
                 "peak_basis": f"{n_sm} SMs x 128 lanes x {sm_max:.0f} MHz ({peak_kind} max clock)"}
-    roof.update(kernel="sweep_kernel", sweep_ms=sweep_avg, reduce_ms=sum(reduce_ms) / len(reduce_ms))
+    kernel = {"ising": "ising_kernel", "random_site": "random_site_kernel"}.get(
+        "ising" if w["bound"] == "alu_ising" else w.get("flags"), "sweep_kernel")
+    roof.update(kernel=kernel, sweep_ms=sweep_avg, reduce_ms=sum(reduce_ms) / len(reduce_ms))
 
     fp64 = None
     if w["fp64_paths"] and not args.no_fp64 and precision == mp.FP32:
         sub = w["fp64_paths"]
-        with mp.Simulation([mp.System(Ls, T, n_paths=sub) for Ls, T, _ in w["systems"]], n_therm, n_meas,
+        with mp.Simulation([mp.System(e[0], e[1], n_paths=sub, lattice=lattice_of(e)) for e in w["systems"]],
+                           n_therm, n_meas,
                            seed=seed, precision=mp.FP64, device=dev) as s64:
             s64.run()
             torch.cuda.synchronize(dev)

@@ -53,6 +53,16 @@ extern "C" {
 /* ---------------------------------------------------------------- enums --- */
 #define MP_LATTICE_SC 0    /* periodic simple cubic, N = L^3, L even */
 #define MP_LATTICE_CHAIN 1 /* open chain, N = L >= 2 */
+#define MP_LATTICE_ISING 2 /* Appendix A: periodic L x L square lattice of Ising
+                              spins s = +-1, N = L^2, L even in 2..MP_ISING_MAX_L;
+                              H = -J sum_bonds s_i s_j - h sum_i s_i.  A batch
+                              is either all Ising or all Heisenberg; precision
+                              and init_mode ANGLES do not apply (the random
+                              start draws each sign with probability 1/2).
+                              Records use the Heisenberg layout with
+                              m_x = m_y = 0, m_z = m; spins (mp_spins) are
+                              (0, 0, s) per site. */
+#define MP_ISING_MAX_L 256
 
 #define MP_FP32 0 /* FP32 spins, dE and Boltzmann factor; FP64 accumulators */
 #define MP_FP64 1 /* FP64 throughout (the plain FP64 GPU form) */
@@ -71,6 +81,18 @@ extern "C" {
                                  wave of its work items, ~2e8 attempts each)
                                  and keep the fastest; ignored when
                                  threads_per_path is set */
+#define MP_FLAG_TWO_START 16u /* Sec. 4's convergence check: in every system the
+                                 first ceil(P/2) paths start from init_mode, the
+                                 other floor(P/2) from the ordered state; the
+                                 estimates report both halves (e_a, e_b, ...) */
+#define MP_FLAG_RANDOM_SITE 32u /* the paper's literal sweep order (Sec. 2.2): a
+                                 sweep is N attempts at sites drawn at random
+                                 (attempt a of sweep s: counter (a, s, path,
+                                 2 | sys<<8), site floor((2 r3 + 1) N / 2^33),
+                                 move from r0..r2).  One thread per path, spins
+                                 in HBM; simple-cubic and chain systems only;
+                                 mp_run_sweeps, mp_checkpoint and mp_restore
+                                 return MP_EINVAL */
 #define MP_FLAG_TEST_STALL 0x100u /* failure injection for tests: streamed paths
                                      never issue their first bulk copy, so the
                                      kernel's bounded wait runs out (about 2 s)
@@ -137,7 +159,12 @@ typedef struct {
   double r_e, r_m, r_mx, r_my, r_mz, r_amz;
   double attempts; /* N x paths x (n_therm + n_meas) */
   double norm_max; /* max over paths of MP_R_NORM */
-  double reserved[11];
+  /* The first ceil(P/2) paths (a) and the other floor(P/2) (b) averaged
+   * separately; with MP_FLAG_TWO_START they started from init_mode and from
+   * the ordered state (Sec. 4).  start_z = max over X in {e, |m|} of
+   * |X_a - X_b| / sqrt(X_a_se^2 + X_b_se^2), skipping an undefined 0/0. */
+  double e_a, e_a_se, e_b, e_b_se, m_a, m_a_se, m_b, m_b_se, start_z;
+  double reserved[2];
 } mp_estimates_t; /* 64 doubles */
 
 #define MP_NEST 64

@@ -8,7 +8,7 @@ threads); ``estimates`` turns its per-path records into the paper's ensemble
 estimates with plain numpy.
 """
 from .oracle import (  # noqa: F401
-    CHAIN, SC, INIT_ANGLES, INIT_ORDERED, INIT_SPHERE, ORDER_CHECKER, ORDER_RANDOM,
+    CHAIN, ISING, SC, TWO_START, INIT_ANGLES, INIT_ORDERED, INIT_SPHERE, ORDER_CHECKER, ORDER_RANDOM,
     REC, NREC, System, build, energy, init, delta_e, philox, run, trial, lib_path,
 )
 from .estimates import estimates, distribution_coefficient  # noqa: F401

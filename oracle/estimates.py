@@ -104,4 +104,20 @@ def estimates(rec: np.ndarray, N: int, T: float) -> dict[str, float]:
     # Eq. (dist-coefficient) on the per-path outputs
     for k in ("e", "m", "mx", "my", "mz", "amz"):
         out["r_" + k] = distribution_coefficient(c[k])
+    # Sec. 4's convergence check: the first ceil(P/2) paths and the other
+    # floor(P/2) averaged separately (with the two-start scheme they started
+    # from the random and from the ordered state); z = the larger of the two
+    # differences (e and |m|) in units of their combined standard error.
+    a = P - P // 2
+    z = []
+    for k in ("e", "m"):
+        for half, rows in (("a", c[k][:a]), ("b", c[k][a:])):
+            out[f"{k}_{half}"] = float(rows.mean()) if rows.size else float("nan")
+            out[f"{k}_{half}_se"] = (float(rows.std(ddof=1) / np.sqrt(rows.size)) if rows.size > 1
+                                     else float("nan"))
+        d = out[f"{k}_a"] - out[f"{k}_b"]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            z.append(np.float64(abs(d)) / np.sqrt(out[f"{k}_a_se"] ** 2 + out[f"{k}_b_se"] ** 2))
+    z = [v for v in z if not np.isnan(v)]  # an undefined ratio (0/0) is skipped
+    out["start_z"] = float(max(z)) if z else float("nan")
     return out

@@ -15,6 +15,8 @@
  *   - Sec. 2.2: Metropolis single spin-flip updates, a lattice sweep of N
  *     attempts, many independent simulation paths from random initial states,
  *     and per-path outputs {M^x, M^y, M^z, H} per lattice site.
+ *   - Appendix A: the same scheme on the square-lattice Ising model
+ *     (run_path_ising, with its own readings).
  *
  * Readings where the paper is silent (each is listed in the design notes):
  *   - trial move: a fresh direction uniform on the sphere, independent of the
@@ -22,7 +24,8 @@
  *   - acceptance: accept when dE <= 0, else accept iff u < exp(-beta dE);
  *   - site order: checkerboard (colour (x+y+z) mod 2 = 0 first, then 1, each
  *     colour in increasing site index).  The paper's "N randomly chosen sites"
- *     order is kept as order_mode = 1 for statistical cross-checks;
+ *     order is order_mode = 1 (one counter per attempt gives the site and the
+ *     move; see run_path);
  *   - random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) with
  *     key = (seed lo, seed hi) and counter = (site, sweep, path, tag | sys<<8);
  *   - per-path output: the mean over n_meas measurement sweeps (n_meas = 1 is
@@ -38,10 +41,12 @@
 
 #define OR_SC 0    /* periodic simple cubic, N = L^3 */
 #define OR_CHAIN 1 /* open chain, N = L */
+#define OR_ISING 2 /* Appendix A: periodic square lattice of Ising spins, N = L^2 */
 
 #define OR_INIT_SPHERE 0  /* uniform on the sphere (Sec. 4 "uniform state") */
 #define OR_INIT_ANGLES 1  /* theta, phi each uniform ("both angles random") */
 #define OR_INIT_ORDERED 2 /* all spins along +z (Sec. 5 ordered start) */
+#define OR_TWO_START 0x100 /* or-ed into init_mode: second half of paths ordered */
 
 #define OR_ORDER_CHECKER 0
 #define OR_ORDER_RANDOM 1
@@ -49,6 +54,7 @@
 #define OR_TAG_UPDATE 0u
 #define OR_TAG_INIT 1u
 #define OR_TAG_SITE 2u
+#define OR_TAG_ISING 4u /* Ising updates: tag 4 + colour */
 
 /* per-path record layout: means over the measurement sweeps, then the final
  * state (the paper's SP output), then bookkeeping */
@@ -101,6 +107,7 @@ static double u01(uint32_t r) { return ((double)r + 0.5) * (1.0 / 4294967296.0);
  * Site i = x + L*(y + L*z).  Neighbour order is fixed: +x, -x, +y, -y, +z, -z
  * with periodic wrap; the chain has i-1 then i+1 where they exist. */
 static int64_t n_sites(int lattice, int L) {
+  if (lattice == OR_ISING) return (int64_t)L * L;
   return lattice == OR_SC ? (int64_t)L * L * L : (int64_t)L;
 }
 
@@ -252,12 +259,14 @@ static void run_path(const path_job* jb) {
   for (int64_t sw = 0; sw < S; ++sw) {
     /* one lattice sweep = N Metropolis attempts */
     if (jb->order_mode == OR_ORDER_RANDOM) {
-      /* the paper's order: N sites drawn at random (Sec. 2.2) */
+      /* the paper's order: N sites drawn at random (Sec. 2.2).  Attempt a
+       * of the sweep takes one counter (a, sweep, path, 2 | sys<<8): the site
+       * is the cell of width 1/N holding u(r[3]), i = floor((2 r3 + 1) N / 2^33)
+       * in exact integer arithmetic, and r[0..2] drive the move as in the
+       * checkerboard order. */
       for (int64_t a = 0; a < N; ++a) {
         oracle_philox((uint32_t)a, (uint32_t)sw, c2, OR_TAG_SITE | sys_hi, jb->k0, jb->k1, r);
-        int64_t i = (int64_t)(u01(r[3]) * (double)N);
-        if (i >= N) i = N - 1;
-        oracle_philox((uint32_t)a, (uint32_t)sw, c2, OR_TAG_UPDATE | sys_hi, jb->k0, jb->k1, r);
+        const int64_t i = (int64_t)((((uint64_t)r[3] * 2u + 1u) * (uint64_t)N) >> 33);
         accepted += metropolis(lat, L, J, hf, beta, s, i, r);
       }
     } else {
@@ -316,6 +325,99 @@ static void run_path(const path_job* jb) {
   free(s);
 }
 
+/* ------------------------------------------------------ 2D Ising path ----
+ * Appendix A runs the same multipath scheme on the square-lattice Ising model.
+ * Readings (the appendix gives no formulas):
+ *   - H = -J sum_bonds s_i s_j - h sum_i s_i, s_i = +-1, periodic L x L, L even;
+ *     site i = x + L y, colour (x + y) mod 2, neighbours +x, -x, +y, -y;
+ *   - random start: s_i = +1 when the top bit of word 0 of the init counter
+ *     (i, 0, path, 1 | sys<<8) is clear, else -1; ordered start: all +1;
+ *   - a sweep flips-tests every colour-0 site, then every colour-1 site;
+ *     dE = 2 s_i (J sum_nb s_j + h), accept when dE <= 0, else iff
+ *     u < exp(-beta dE) with u = (r + 1/2) 2^-32;
+ *   - the word r of the colour-c site with half index hh = i >> 1 is word
+ *     hh mod 4 of Philox(hh / 4, sweep, path, (4 + c) | sys<<8): one call
+ *     serves four sites of one colour;
+ *   - per sweep: e = H / N and m = sum s_i / N; the record keeps the
+ *     Heisenberg layout with m_x = m_y = 0 and m_z = m. */
+static void run_path_ising(const path_job* jb) {
+  const oracle_system* sy = jb->sys;
+  const int L = sy->L;
+  const int64_t N = (int64_t)L * L;
+  const double beta = 1.0 / sy->T, J = sy->J, hf = sy->h;
+  const uint32_t c2 = (uint32_t)jb->path;
+  const uint32_t sys_hi = (uint32_t)jb->sys_index << 8;
+  int* s = (int*)malloc(sizeof(int) * N);
+  uint32_t r[4];
+  for (int64_t i = 0; i < N; ++i) {
+    oracle_philox((uint32_t)i, 0u, c2, OR_TAG_INIT | sys_hi, jb->k0, jb->k1, r);
+    s[i] = (jb->init_mode == OR_INIT_ORDERED) ? 1 : ((r[0] >> 31) ? -1 : 1);
+  }
+  double acc[NREC];
+  memset(acc, 0, sizeof(acc));
+  int64_t accepted = 0;
+  const int64_t S = jb->n_therm + jb->n_meas;
+  for (int64_t sw = 0; sw < S; ++sw) {
+    for (int c = 0; c < 2; ++c) {
+      for (int64_t i = 0; i < N; ++i) {
+        const int64_t x = i % L, y = i / L;
+        if (((x + y) & 1) != c) continue;
+        const int64_t hh = i >> 1;
+        oracle_philox((uint32_t)(hh >> 2), (uint32_t)sw, c2, (OR_TAG_ISING + (uint32_t)c) | sys_hi,
+                      jb->k0, jb->k1, r);
+        const int64_t nb[4] = {(x + 1) % L + L * y, (x + L - 1) % L + L * y,
+                               x + L * ((y + 1) % L), x + L * ((y + L - 1) % L)};
+        const int hloc = s[nb[0]] + s[nb[1]] + s[nb[2]] + s[nb[3]];
+        const double dE = 2.0 * (double)s[i] * (J * (double)hloc + hf);
+        if (dE <= 0.0 || u01(r[hh & 3]) < exp(-beta * dE)) {
+          s[i] = -s[i];
+          ++accepted;
+        }
+      }
+    }
+    if (sw >= jb->n_therm) {
+      int64_t bonds = 0, msum = 0;
+      for (int64_t i = 0; i < N; ++i) {
+        const int64_t x = i % L, y = i / L;
+        bonds += (int64_t)s[i] * (s[(x + 1) % L + L * y] + s[x + L * ((y + 1) % L)]);
+        msum += s[i];
+      }
+      const double e = (-J * (double)bonds - hf * (double)msum) / (double)N;
+      const double mz = (double)msum / (double)N;
+      const double m = fabs(mz);
+      acc[R_E] += e;
+      acc[R_E2] += e * e;
+      acc[R_M] += m;
+      acc[R_M2] += m * m;
+      acc[R_M4] += m * m * m * m;
+      acc[R_MZ] += mz;
+      acc[R_MZ2] += mz * mz;
+      acc[R_AMZ] += m;
+      acc[R_EM] += e * m;
+      acc[R_EMZ] += e * mz;
+      acc[R_MMZ] += m * mz;
+      if (sw == S - 1) {
+        acc[R_FMZ] = mz; acc[R_FE] = e;
+      }
+    }
+  }
+  double* out = jb->rec;
+  for (int k = R_E; k <= R_MMZ; ++k) out[k] = acc[k] / (double)jb->n_meas;
+  out[R_FMX] = 0.0; out[R_FMY] = 0.0;
+  out[R_FMZ] = acc[R_FMZ]; out[R_FE] = acc[R_FE];
+  out[R_ACC] = (double)accepted / ((double)S * (double)N);
+  out[R_NORM] = 0.0;
+  out[R_SPARE] = 0.0;
+  if (jb->spins_out) {
+    for (int64_t i = 0; i < N; ++i) {
+      jb->spins_out[3 * i + 0] = 0.0;
+      jb->spins_out[3 * i + 1] = 0.0;
+      jb->spins_out[3 * i + 2] = (double)s[i];
+    }
+  }
+  free(s);
+}
+
 /* ------------------------------------------------------------ threads ---- */
 typedef struct {
   path_job* jobs;
@@ -331,7 +433,10 @@ static void* worker(void* arg) {
     int64_t j = q->next++;
     pthread_mutex_unlock(&q->mu);
     if (j >= q->n_jobs) return NULL;
-    run_path(&q->jobs[j]);
+    if (q->jobs[j].sys->lattice == OR_ISING)
+      run_path_ising(&q->jobs[j]);
+    else
+      run_path(&q->jobs[j]);
   }
 }
 
@@ -347,7 +452,8 @@ int oracle_run(const oracle_system* sys, int n_sys, int64_t n_therm, int64_t n_m
   int64_t total = 0;
   for (int k = 0; k < n_sys; ++k) {
     const oracle_system* sy = &sys[k];
-    if (sy->lattice != OR_SC && sy->lattice != OR_CHAIN) return -1;
+    if (sy->lattice != OR_SC && sy->lattice != OR_CHAIN && sy->lattice != OR_ISING) return -1;
+    if (sy->lattice == OR_ISING && ((sy->L & 1) || order_mode != OR_ORDER_CHECKER)) return -1;
     if (sy->L < 2 || !(sy->T > 0.0) || sy->n_paths <= 0) return -1;
     if (sy->lattice == OR_SC && (sy->L & 1) && order_mode == OR_ORDER_CHECKER) return -1;
     if (sy->path_begin < 0 || sy->path_count < 0 ||
@@ -367,7 +473,12 @@ int oracle_run(const oracle_system* sys, int n_sys, int64_t n_therm, int64_t n_m
       jobs[j].n_meas = n_meas;
       jobs[j].k0 = (uint32_t)(seed & 0xffffffffu);
       jobs[j].k1 = (uint32_t)(seed >> 32);
-      jobs[j].init_mode = init_mode;
+      /* Sec. 4's convergence check: with OR_TWO_START the first ceil(P/2)
+       * paths start from init_mode, the other floor(P/2) from the ordered
+       * state, and the two halves are averaged separately. */
+      jobs[j].init_mode = init_mode & 0xff;
+      if ((init_mode & OR_TWO_START) && jobs[j].path >= sys[k].n_paths - sys[k].n_paths / 2)
+        jobs[j].init_mode = OR_INIT_ORDERED;
       jobs[j].order_mode = order_mode;
       jobs[j].rec = records + j * NREC;
       jobs[j].spins_out = spins_out ? spins_out + spin_off : NULL;

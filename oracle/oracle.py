@@ -17,9 +17,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "mp_oracle.c")
 lib_path = os.path.join(HERE, "libmp_oracle.so")
 
-SC, CHAIN = 0, 1
+SC, CHAIN, ISING = 0, 1, 2  # ISING: periodic L x L square lattice of +-1 spins (Appendix A)
 INIT_SPHERE, INIT_ANGLES, INIT_ORDERED = 0, 1, 2
 ORDER_CHECKER, ORDER_RANDOM = 0, 1
+TWO_START = 0x100  # or-ed into init_mode by run(two_start=True)
 
 # per-path record fields, in the order mp_oracle.c writes them
 REC = dict(
@@ -62,6 +63,8 @@ class System:
 
     @property
     def N(self) -> int:
+        if self.lattice == ISING:
+            return self.L ** 2
         return self.L ** 3 if self.lattice == SC else self.L
 
     def count(self) -> int:
@@ -155,8 +158,11 @@ def delta_e(lattice: int, L: int, J: float, h: float, spins: np.ndarray, i: int,
 
 def run(systems: list[System], n_therm: int, n_meas: int, seed: int = 1,
         init_mode: int = INIT_SPHERE, order_mode: int = ORDER_CHECKER,
-        threads: int | None = None, want_spins: bool = False):
+        threads: int | None = None, want_spins: bool = False, two_start: bool = False):
     """Run the requested paths of every system.
+
+    With ``two_start`` (Sec. 4's convergence check) the first ceil(P/2) paths
+    of each system start from ``init_mode`` and the rest from the ordered state.
 
     Returns a list (one entry per system) of per-path records shaped
     (path_count, NREC); with ``want_spins`` also the final spins of each path,
@@ -174,7 +180,8 @@ def run(systems: list[System], n_therm: int, n_meas: int, seed: int = 1,
     spins = np.zeros(max(spin_total, 1)) if want_spins else None
     if threads is None:
         threads = os.cpu_count() or 1
-    rc = lib.oracle_run(arr, len(systems), n_therm, n_meas, seed, init_mode, order_mode,
+    mode = init_mode | (TWO_START if two_start else 0)
+    rc = lib.oracle_run(arr, len(systems), n_therm, n_meas, seed, mode, order_mode,
                         threads, _dptr(rec), _dptr(spins) if want_spins else None)
     if rc != 0:
         raise ValueError("oracle_run rejected its arguments")

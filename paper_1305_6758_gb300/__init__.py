@@ -22,10 +22,11 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmp.so")
 
-SC, CHAIN = 0, 1
+SC, CHAIN, ISING = 0, 1, 2  # ISING: periodic L x L square lattice of +-1 spins (Appendix A)
 FP32, FP64 = 0, 1
 INIT_SPHERE, INIT_ANGLES, INIT_ORDERED = 0, 1, 2
-FLAG_GRAPH, FLAG_KEEP_SPINS, FLAG_STREAM, FLAG_AUTOTUNE, FLAG_TEST_STALL = 1, 2, 4, 8, 0x100
+FLAG_GRAPH, FLAG_KEEP_SPINS, FLAG_STREAM, FLAG_AUTOTUNE, FLAG_TWO_START, FLAG_RANDOM_SITE = 1, 2, 4, 8, 16, 32
+FLAG_TEST_STALL = 0x100
 
 MP_OK, MP_EINVAL, MP_ENOMEM, MP_ECUDA, MP_ESTATE, MP_ECANCELED, MP_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 
@@ -85,11 +86,12 @@ EST_FIELDS = [
     "cv_m",
     "r_e", "r_m", "r_mx", "r_my", "r_mz", "r_amz",
     "attempts", "norm_max",
+    "e_a", "e_a_se", "e_b", "e_b_se", "m_a", "m_a_se", "m_b", "m_b_se", "start_z",
 ]
 
 
 class MPEstimates(ctypes.Structure):
-    _fields_ = [(f, ctypes.c_double) for f in EST_FIELDS] + [("reserved", ctypes.c_double * 11)]
+    _fields_ = [(f, ctypes.c_double) for f in EST_FIELDS] + [("reserved", ctypes.c_double * 2)]
 
 
 assert ctypes.sizeof(MPEstimates) == NEST * 8
@@ -191,6 +193,8 @@ class System:
 
     @property
     def N(self) -> int:
+        if self.lattice == ISING:
+            return self.L ** 2
         return self.L ** 3 if self.lattice == SC else self.L
 
 

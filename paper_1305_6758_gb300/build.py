@@ -22,7 +22,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 # per-file extra flags: the FP32 sweep flushes denormals (its uniforms are >= 2^-24)
 EXTRA = {"sweep_fp32.cu": ["-ftz=true"]}
-SOURCES = ["mp_api.cu", "reduce.cu", "sweep_fp32.cu", "sweep_fp64.cu", "noalloc.cu"]
+SOURCES = ["mp_api.cu", "reduce.cu", "sweep_fp32.cu", "sweep_fp64.cu", "ising.cu", "random_site.cu",
+           "noalloc.cu"]
 
 
 def nvcc() -> str:

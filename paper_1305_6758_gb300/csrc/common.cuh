@@ -9,10 +9,21 @@ namespace mpk {
 
 constexpr uint32_t kTagUpdate = 0u;  // counter tag of the sweep updates
 constexpr uint32_t kTagInit = 1u;    // counter tag of the initial state
+constexpr uint32_t kTagIsing = 4u;   // Ising flip tests: tag 4 + colour
+constexpr int32_t kTwoStart = 0x100; // or-ed into SweepParams::init_mode (MP_FLAG_TWO_START)
+
+// Start of one path: with the two-start scheme (Sec. 4) the last floor(P/2)
+// paths of a system start from the ordered state.
+__host__ __device__ inline int path_init_mode(int32_t mode, int64_t path, int64_t n_paths) {
+  return ((mode & kTwoStart) && path >= n_paths - n_paths / 2) ? MP_INIT_ORDERED : (mode & 0xff);
+}
 
 constexpr int kAccDoubles = 24;      // FP64 per-path accumulators (>= MP_NREC) in shared memory
 constexpr int kRedSlots = 4;         // doubles per warp in the per-sweep reduction
 constexpr int kMaxCta = 1024;
+// Most paths one CTA can hold: one warp each (groups of more than one warp
+// are limited to 15 by the named barriers 1..15).
+constexpr int kMaxGroups = kMaxCta / 32;
 
 // One system (lattice, size, temperature, couplings) of a batch, with the
 // launch shape the planner chose for it.
@@ -67,6 +78,7 @@ struct SweepParams {
   const int64_t* state_stride;  // bytes per path, per system
   int32_t resume, save;
   const volatile int* cancel;   // host-mapped cancel flag, or nullptr
+  const unsigned long long* ising_thr;  // Ising: 10 acceptance thresholds per system
 };
 
 constexpr int kErrTimeout = 1;

@@ -35,6 +35,22 @@ cudaError_t sweep_occupancy(int precision, int variant, int cta, int smem, int* 
 cudaError_t launch_sweep(int precision, int variant, const SweepParams& p, int grid, int cta,
                          int smem, cudaStream_t st);
 
+// The square-lattice Ising kernel (variant kIsingKernel), any even L.
+constexpr int kIsingKernel = -3;
+cudaError_t ising_prepare(int device, int* max_dynamic, int* max_threads);
+cudaError_t ising_occupancy(int cta, int smem, int* blocks);
+cudaError_t launch_ising(const SweepParams& p, int grid, int cta, int smem, cudaStream_t st);
+// Slice bytes of an Ising path: thresholds (128 bytes) then one byte per spin.
+constexpr int kIsingThrBytes = 128;
+
+// The random-site order (MP_FLAG_RANDOM_SITE, variant kRandomSiteKernel): one
+// thread per path, lattices in HBM (random_site_bytes_per_site bytes per site
+// and path).
+constexpr int kRandomSiteKernel = -4;
+int random_site_bytes_per_site(int precision);
+cudaError_t launch_random_site(int precision, const SweepParams& p, int n_systems, int64_t total_paths,
+                               void* lattice, int64_t elements, cudaStream_t st);
+
 cudaError_t reduce_prepare();  // raise the dynamic shared memory limit
 cudaError_t launch_reduce(const ReduceParams& p, int n_systems, int64_t max_paths, cudaStream_t st);
 cudaError_t launch_backward(const BackwardParams& p, int n_systems, cudaStream_t st);

@@ -36,15 +36,18 @@ bool sweep_supports_L(int precision, int L) {
 }
 cudaError_t sweep_prepare(int precision, int variant, int device, int* max_dynamic,
                           int* max_threads) {
+  if (variant == kIsingKernel) return ising_prepare(device, max_dynamic, max_threads);
   return precision == MP_FP64 ? sweep_prepare_fp64(variant, device, max_dynamic, max_threads)
                               : sweep_prepare_fp32(variant, device, max_dynamic, max_threads);
 }
 cudaError_t sweep_occupancy(int precision, int variant, int cta, int smem, int* blocks) {
+  if (variant == kIsingKernel) return ising_occupancy(cta, smem, blocks);
   return precision == MP_FP64 ? sweep_occupancy_fp64(variant, cta, smem, blocks)
                               : sweep_occupancy_fp32(variant, cta, smem, blocks);
 }
 cudaError_t launch_sweep(int precision, int variant, const SweepParams& p, int grid, int cta,
                          int smem, cudaStream_t st) {
+  if (variant == kIsingKernel) return launch_ising(p, grid, cta, smem, st);
   return precision == MP_FP64 ? launch_sweep_fp64(variant, p, grid, cta, smem, st)
                               : launch_sweep_fp32(variant, p, grid, cta, smem, st);
 }
@@ -58,7 +61,36 @@ namespace {
 thread_local std::string g_create_error;
 
 int64_t sites_of(const mp_system& s) {
+  if (s.lattice == MP_LATTICE_ISING) return static_cast<int64_t>(s.L) * s.L;
   return s.lattice == MP_LATTICE_SC ? static_cast<int64_t>(s.L) * s.L * s.L : s.L;
+}
+
+// Shared-memory bytes of one path's spins (both colours) in the sweep kernels.
+int64_t lattice_bytes(const mp_system& s, int real) {
+  const int64_t NH = (sites_of(s) + 1) / 2;
+  if (s.lattice == MP_LATTICE_ISING) return kIsingThrBytes + 2 * NH;
+  return 6 * NH * real;
+}
+
+// Ising acceptance as an integer test on a Philox word r (Appendix A kernel):
+// accept iff r < t with t = #{r : (r + 1/2) 2^-32 < exp(-beta dE)}, for
+// dE = 2 s (J k + h), s = +1 (entries 0..4) and -1 (5..9), neighbour sum
+// k = -4, -2, 0, 2, 4; dE <= 0 is always accepted (t = 2^32).  (r + 1/2) 2^-32
+// and p 2^32 are exact in FP64, so r + 1/2 < p 2^32 <=> r < ceil(p 2^32 - 1/2).
+void ising_thresholds(const mp_system& s, unsigned long long* t) {
+  const double beta = 1.0 / s.T;
+  for (int a = 0; a < 2; ++a) {
+    const double sg = a == 0 ? 1.0 : -1.0;
+    for (int k = 0; k < 5; ++k) {
+      const double dE = 2.0 * sg * (s.J * static_cast<double>(2 * k - 4) + s.h);
+      unsigned long long v = 1ull << 32;
+      if (dE > 0.0) {
+        const double y = std::exp(-beta * dE) * 4294967296.0 - 0.5;
+        v = y <= 0.0 ? 0ull : std::min<unsigned long long>(static_cast<unsigned long long>(std::ceil(y)), 1ull << 32);
+      }
+      t[a * 5 + k] = v;
+    }
+  }
 }
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
@@ -104,6 +136,7 @@ struct mp_state {
   double* d_est = nullptr;
   double* d_spins = nullptr;
   int64_t* d_spin_offset = nullptr;
+  unsigned long long* d_thr = nullptr;  // Ising acceptance thresholds, 10 per system
   int* d_error = nullptr;          // nonzero when a bounded wait in a kernel gave up
   void* d_lattice = nullptr;       // HBM lattices of streamed paths
   size_t lattice_capacity = 0;     // bytes allocated at d_lattice
@@ -223,8 +256,12 @@ int validate(const mp_config* cfg) {
     return fail(nullptr, MP_EINVAL, "threads_per_path must be a multiple of 32 in 32..1024");
   for (int k = 0; k < cfg->n_systems; ++k) {
     const mp_system& s = cfg->systems[k];
-    if (s.lattice != MP_LATTICE_SC && s.lattice != MP_LATTICE_CHAIN)
+    if (s.lattice != MP_LATTICE_SC && s.lattice != MP_LATTICE_CHAIN && s.lattice != MP_LATTICE_ISING)
       return fail(nullptr, MP_EINVAL, "system %d: unknown lattice %d", k, s.lattice);
+    if ((s.lattice == MP_LATTICE_ISING) != (cfg->systems[0].lattice == MP_LATTICE_ISING))
+      return fail(nullptr, MP_EINVAL, "Ising and Heisenberg systems cannot share a batch");
+    if (s.lattice == MP_LATTICE_ISING && (cfg->flags & MP_FLAG_RANDOM_SITE))
+      return fail(nullptr, MP_EINVAL, "the random-site order is built for Heisenberg systems only");
     if (!(s.T > 0.0) || !std::isfinite(s.T) || !std::isfinite(s.J) || !std::isfinite(s.h))
       return fail(nullptr, MP_EINVAL, "system %d: need finite T > 0, J, h", k);
     if (s.n_paths < 1 || s.n_paths > 0x7fffffffLL)
@@ -233,6 +270,9 @@ int validate(const mp_config* cfg) {
       if (s.L < 2 || (s.L & 1))
         return fail(nullptr, MP_EINVAL, "system %d: simple cubic L must be even and >= 2", k);
       if (s.L > 1024) return fail(nullptr, MP_EINVAL, "system %d: L=%d above 1024", k, s.L);
+    } else if (s.lattice == MP_LATTICE_ISING) {
+      if (s.L < 2 || (s.L & 1) || s.L > MP_ISING_MAX_L)
+        return fail(nullptr, MP_EINVAL, "system %d: Ising L must be even in 2..%d", k, MP_ISING_MAX_L);
     } else if (s.L < 2 || s.L > 8192) {
       return fail(nullptr, MP_EINVAL, "system %d: chain length must be in 2..8192", k);
     }
@@ -244,7 +284,10 @@ int validate(const mp_config* cfg) {
 // thread per half-sweep), paths per CTA from the CTA size, the named-barrier
 // budget and shared memory; the CTA shrinks while there are too few work
 // items to cover every SM twice.
+int plan_random_site(mp_state* h);
+
 int plan(mp_state* h, const mp_config* cfg) {
+  if (h->flags & MP_FLAG_RANDOM_SITE) return plan_random_site(h);
   const int real = h->precision == MP_FP64 ? 8 : 4;
   const int n = static_cast<int>(h->systems.size());
   h->lattice_groups = 0;
@@ -253,6 +296,7 @@ int plan(mp_state* h, const mp_config* cfg) {
   // one kernel per lattice size when the batch has a single size; lattices
   // too large for shared memory are streamed from HBM (any size, one kernel)
   auto variant_of = [&](const mp_system& sy) {
+    if (sy.lattice == MP_LATTICE_ISING) return kIsingKernel;
     if (sy.lattice == MP_LATTICE_CHAIN) return -1;
     return streamed(sy, h->precision, h->flags) ? -2 : sy.L;
   };
@@ -315,10 +359,11 @@ int plan(mp_state* h, const mp_config* cfg) {
     tp[k] = t;
     // partial-sum ring: the largest power of two up to 16 sweeps that fits
     ring[k] = 16;
-    slice[k] = round_up(slice_spin_offset(t, ring[k]) + 6 * NH * real, 128);
+    const int64_t lat = lattice_bytes(h->systems[k], real);
+    slice[k] = static_cast<int>(std::min<int64_t>(INT32_MAX / 2, round_up(slice_spin_offset(t, ring[k]) + lat, 128)));
     while (ring[k] > 1 && slice[k] > smem_max) {
       ring[k] /= 2;
-      slice[k] = round_up(slice_spin_offset(t, ring[k]) + 6 * NH * real, 128);
+      slice[k] = static_cast<int>(std::min<int64_t>(INT32_MAX / 2, round_up(slice_spin_offset(t, ring[k]) + lat, 128)));
     }
     if (slice[k] > smem_max)
       return fail(h, MP_EINVAL, "system %d needs %d bytes of shared memory per path (max %d)", k,
@@ -402,6 +447,52 @@ int plan(mp_state* h, const mp_config* cfg) {
   return MP_OK;
 }
 
+// The random-site order: one thread per path (128-thread CTAs), every path's
+// lattice in HBM; no work items.
+int plan_random_site(mp_state* h) {
+  const int n = static_cast<int>(h->systems.size());
+  h->variant = kRandomSiteKernel;
+  h->hsys.resize(n);
+  h->items.clear();
+  h->spin_offset.assign(n, 0);
+  h->max_paths = 0;
+  int64_t rec = 0, spins = 0;
+  for (int k = 0; k < n; ++k) {
+    const mp_system& s = h->systems[k];
+    DevSystem& d = h->hsys[k];
+    d = DevSystem{};
+    d.lattice = s.lattice;
+    d.L = s.L;
+    d.N = static_cast<int32_t>(sites_of(s));
+    d.NH = (d.N + 1) / 2;
+    d.tp = 1;
+    d.g = 1;
+    d.ring = 1;
+    d.T = s.T;
+    d.J = s.J;
+    d.h = s.h;
+    d.beta = 1.0 / s.T;
+    d.rec_offset = rec;
+    d.n_paths = s.n_paths;
+    d.mode = kModeShared;
+    rec += s.n_paths;
+    h->spin_offset[k] = spins;
+    spins += s.n_paths * 3 * static_cast<int64_t>(d.N);
+    h->max_paths = std::max(h->max_paths, s.n_paths);
+  }
+  h->total_paths = rec;
+  h->total_spins = spins;
+  h->cta = 128;
+  h->smem = 0;
+  const int64_t grid = (rec + 127) / 128;
+  if (grid > 0x7fffffffLL) return fail(h, MP_EINVAL, "too many paths");
+  h->grid = static_cast<int>(grid);
+  h->lattice_groups = 0;
+  h->lattice_stride = 0;
+  MP_CUDA(h, reduce_prepare());
+  return MP_OK;
+}
+
 // One run of sweeps [s_begin, s_end) of the schedule, then the reduction.
 int enqueue_run(mp_state* h, int64_t s_begin, int64_t s_end, bool resume, bool save,
                 bool capturing = false) {
@@ -413,12 +504,13 @@ int enqueue_run(mp_state* h, int64_t s_begin, int64_t s_end, bool resume, bool s
   p.spins = h->d_spins;
   p.spin_offset = h->d_spin_offset;
   p.n_items = static_cast<int32_t>(h->items.size());
-  p.init_mode = h->init_mode;
+  p.init_mode = h->init_mode | ((h->flags & MP_FLAG_TWO_START) ? kTwoStart : 0);
   p.key = philox_round_keys(h->seed);
   p.lattice = h->d_lattice;
   p.lattice_stride = h->lattice_stride;
   p.lattice_groups = h->lattice_groups;
   p.error = h->d_error;
+  p.ising_thr = h->d_thr;
   p.test_stall = (h->flags & MP_FLAG_TEST_STALL) ? 1u : 0u;
   p.s_begin = s_begin;
   p.s_end = s_end;
@@ -440,7 +532,11 @@ int enqueue_run(mp_state* h, int64_t s_begin, int64_t s_end, bool resume, bool s
   MP_CUDA(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int), h->stream));
   MP_CUDA(h, cudaMemsetAsync(h->d_error, 0, sizeof(int), h->stream));
   MP_CUDA(h, cudaEventRecordWithFlags(h->ev[0], h->stream, evflag));
-  MP_CUDA(h, launch_sweep(h->precision, h->variant, p, h->grid, h->cta, h->smem, h->stream));
+  if (h->variant == kRandomSiteKernel)
+    MP_CUDA(h, launch_random_site(h->precision, p, static_cast<int>(h->hsys.size()), h->total_paths,
+                                  h->d_lattice, h->total_spins / 3, h->stream));
+  else
+    MP_CUDA(h, launch_sweep(h->precision, h->variant, p, h->grid, h->cta, h->smem, h->stream));
   MP_CUDA(h, cudaEventRecordWithFlags(h->ev[1], h->stream, evflag));
   MP_CUDA(h, launch_reduce(r, static_cast<int>(h->hsys.size()), h->max_paths, h->stream));
   MP_CUDA(h, cudaEventRecordWithFlags(h->ev[2], h->stream, evflag));
@@ -451,9 +547,14 @@ int enqueue_run(mp_state* h, int64_t s_begin, int64_t s_end, bool resume, bool s
 
 // The HBM lattice buffers of the current plan (streamed paths), grown on demand.
 int ensure_lattice(mp_state* h) {
-  if (h->lattice_groups == 0) return MP_OK;
-  h->lattice_stride = (h->lattice_stride + 255) / 256 * 256;
-  const size_t need = static_cast<size_t>(h->grid) * h->lattice_groups * h->lattice_stride;
+  size_t need = 0;
+  if (h->variant == kRandomSiteKernel) {  // every path's lattice
+    need = static_cast<size_t>(h->total_spins / 3) * random_site_bytes_per_site(h->precision);
+  } else {
+    if (h->lattice_groups == 0) return MP_OK;
+    h->lattice_stride = (h->lattice_stride + 255) / 256 * 256;
+    need = static_cast<size_t>(h->grid) * h->lattice_groups * h->lattice_stride;
+  }
   if (need <= h->lattice_capacity) return MP_OK;
   MP_CUDA(h, cudaStreamSynchronize(h->stream));
   dev_free(h, h->d_lattice);
@@ -470,6 +571,11 @@ int upload_tables(mp_state* h, const std::vector<WorkItem>& items) {
   MP_CUDA(h, cudaMemcpyAsync(h->d_items, items.data(), sizeof(WorkItem) * items.size(),
                              cudaMemcpyHostToDevice, h->stream));
   MP_CUDA(h, cudaMemcpyAsync(h->d_spin_offset, h->spin_offset.data(), sizeof(int64_t) * n,
+                             cudaMemcpyHostToDevice, h->stream));
+  std::vector<unsigned long long> thr(10 * static_cast<size_t>(n), 0ull);
+  for (int k = 0; k < n; ++k)
+    if (h->systems[k].lattice == MP_LATTICE_ISING) ising_thresholds(h->systems[k], &thr[10 * k]);
+  MP_CUDA(h, cudaMemcpyAsync(h->d_thr, thr.data(), sizeof(unsigned long long) * thr.size(),
                              cudaMemcpyHostToDevice, h->stream));
   MP_CUDA(h, cudaStreamSynchronize(h->stream));
   return MP_OK;
@@ -496,7 +602,7 @@ double calibrate(mp_state* h, int k) {
   p.queue = h->d_queue;
   p.records = h->d_rec;
   p.n_items = static_cast<int32_t>(sub.size());
-  p.init_mode = h->init_mode;
+  p.init_mode = h->init_mode | ((h->flags & MP_FLAG_TWO_START) ? kTwoStart : 0);
   p.n_therm = sweeps - 1;
   p.n_meas = 1;
   p.s_begin = 0;
@@ -506,6 +612,7 @@ double calibrate(mp_state* h, int k) {
   p.lattice_stride = h->lattice_stride;
   p.lattice_groups = h->lattice_groups;
   p.error = h->d_error;
+  p.ising_thr = h->d_thr;
   float ms = 0.f;
   if (cudaMemsetAsync(h->d_queue, 0, sizeof(int), h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->d_error, 0, sizeof(int), h->stream) != cudaSuccess ||
@@ -665,7 +772,9 @@ int mp_create_ex(const mp_config* cfg, mp_handle* out) {
   h->d_rec = static_cast<double*>(dev_alloc(h, sizeof(double) * MP_NREC * h->total_paths));
   h->d_est = static_cast<double*>(dev_alloc(h, sizeof(double) * MP_NEST * n));
   h->d_spin_offset = static_cast<int64_t*>(dev_alloc(h, sizeof(int64_t) * n));
-  if (!h->d_sys || !h->d_items || !h->d_queue || !h->d_rec || !h->d_est || !h->d_spin_offset)
+  h->d_thr = static_cast<unsigned long long*>(dev_alloc(h, sizeof(unsigned long long) * 10 * n));
+  if (!h->d_sys || !h->d_items || !h->d_queue || !h->d_rec || !h->d_est || !h->d_spin_offset ||
+      !h->d_thr)
     return bail(fail(h, MP_ENOMEM, "device allocation failed"));
   h->d_error = static_cast<int*>(dev_alloc(h, 256));
   if (!h->d_error) return bail(fail(h, MP_ENOMEM, "device allocation failed"));
@@ -673,7 +782,7 @@ int mp_create_ex(const mp_config* cfg, mp_handle* out) {
     h->d_spins = static_cast<double*>(dev_alloc(h, sizeof(double) * h->total_spins));
     if (!h->d_spins) return bail(fail(h, MP_ENOMEM, "spin buffer allocation failed"));
   }
-  if ((h->flags & MP_FLAG_AUTOTUNE) && cfg->threads_per_path == 0) {
+  if ((h->flags & MP_FLAG_AUTOTUNE) && cfg->threads_per_path == 0 && !(h->flags & MP_FLAG_RANDOM_SITE)) {
     rc = autotune(h, cfg);
     if (rc != MP_OK) return bail(rc);
   }
@@ -831,7 +940,7 @@ int ensure_state(mp_state* h) {
     const DevSystem& d = h->hsys[k];
     const int64_t spins = d.mode == kModeStreamed
                               ? static_cast<int64_t>(2) * d.L * half_plane_bytes(d.L, real)
-                              : static_cast<int64_t>(6) * d.NH * real;
+                              : lattice_bytes(h->systems[k], real);
     h->state_stride[k] = (kStateHeader + spins + 255) / 256 * 256;
     h->state_offset[k] = off;
     off += h->state_stride[k] * d.n_paths;
@@ -890,6 +999,7 @@ extern "C" {
 
 int mp_run_sweeps(mp_handle h, int64_t n_sweeps) {
   if (!h) return fail(nullptr, MP_EINVAL, "handle is NULL");
+  if (h->flags & MP_FLAG_RANDOM_SITE) return fail(h, MP_EINVAL, "random-site runs are not resumable");
   const int64_t total = h->n_therm + h->n_meas;
   if (n_sweeps < 1) return fail(h, MP_EINVAL, "n_sweeps must be >= 1");
   if (h->sweeps_done >= total) return fail(h, MP_ESTATE, "the schedule of %lld sweeps is complete",
@@ -917,6 +1027,7 @@ int mp_progress(mp_handle h, int64_t* sweeps_done) {
 
 int mp_checkpoint(mp_handle h, void* buf, size_t* nbytes) {
   if (!h || !nbytes) return fail(h, MP_EINVAL, "NULL argument");
+  if (h->flags & MP_FLAG_RANDOM_SITE) return fail(h, MP_EINVAL, "random-site runs are not resumable");
   if (h->sweeps_done == 0 || !h->d_state) return fail(h, MP_ESTATE, "nothing to checkpoint (no mp_run_sweeps yet)");
   const size_t need = sizeof(CheckpointHeader) + static_cast<size_t>(h->state_bytes);
   if (!buf) {
@@ -941,6 +1052,7 @@ int mp_checkpoint(mp_handle h, void* buf, size_t* nbytes) {
 
 int mp_restore(mp_handle h, const void* buf, size_t nbytes) {
   if (!h || !buf) return fail(h, MP_EINVAL, "NULL argument");
+  if (h->flags & MP_FLAG_RANDOM_SITE) return fail(h, MP_EINVAL, "random-site runs are not resumable");
   if (nbytes < sizeof(CheckpointHeader)) return fail(h, MP_EINVAL, "checkpoint too short");
   CheckpointHeader hd;
   std::memcpy(&hd, buf, sizeof(hd));

@@ -202,6 +202,33 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const ReduceParams 
     block_sum<kNumDerived>(jk_var, scratch);
   }
 
+  // The two halves of the paths (Sec. 4's two-start check): paths
+  // 0 .. Pa-1 and Pa .. P-1 with Pa = ceil(P/2); sums, then variances, of e
+  // and |m| over each half.
+  const int64_t Pa = P - P / 2, Pb = P / 2;
+  double hs[4] = {0.0, 0.0, 0.0, 0.0};  // e_a, m_a, e_b, m_b
+  for (int64_t i = threadIdx.x; i < P; i += blockDim.x) {
+    const double* r = rec + i * MP_NREC;
+    const bool a = i < Pa;
+    hs[0] += a ? r[MP_R_E] : 0.0;
+    hs[1] += a ? r[MP_R_M] : 0.0;
+    hs[2] += a ? 0.0 : r[MP_R_E];
+    hs[3] += a ? 0.0 : r[MP_R_M];
+  }
+  block_sum<4>(hs, scratch);
+  const double hmu[4] = {hs[0] / Pa, hs[1] / Pa, Pb ? hs[2] / Pb : NAN, Pb ? hs[3] / Pb : NAN};
+  double hv[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t i = threadIdx.x; i < P; i += blockDim.x) {
+    const double* r = rec + i * MP_NREC;
+    const bool a = i < Pa;
+    const double de = r[MP_R_E] - (a ? hmu[0] : hmu[2]), dm = r[MP_R_M] - (a ? hmu[1] : hmu[3]);
+    hv[0] += a ? de * de : 0.0;
+    hv[1] += a ? dm * dm : 0.0;
+    hv[2] += a ? 0.0 : de * de;
+    hv[3] += a ? 0.0 : dm * dm;
+  }
+  block_sum<4>(hv, scratch);
+
   // pass 5: distribution coefficients of the per-path outputs
   const int rfield[6] = {MP_R_E, MP_R_M, MP_R_MX, MP_R_MY, MP_R_MZ, MP_R_AMZ};
   double rcoef[6];
@@ -250,7 +277,17 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const ReduceParams 
     o->r_amz = rcoef[5];
     o->attempts = N * static_cast<double>(P) * static_cast<double>(p.n_therm + p.n_meas);
     o->norm_max = worst;
-    for (int k = 0; k < 11; ++k) o->reserved[k] = 0.0;
+    auto hse = [&](int k, int64_t n) {
+      return n >= 2 ? sqrt(hv[k] / (static_cast<double>(n) * static_cast<double>(n - 1))) : NAN;
+    };
+    o->e_a = hmu[0];  o->e_a_se = hse(0, Pa);
+    o->m_a = hmu[1];  o->m_a_se = hse(1, Pa);
+    o->e_b = hmu[2];  o->e_b_se = hse(2, Pb);
+    o->m_b = hmu[3];  o->m_b_se = hse(3, Pb);
+    const double ze = fabs(o->e_a - o->e_b) / sqrt(o->e_a_se * o->e_a_se + o->e_b_se * o->e_b_se);
+    const double zm = fabs(o->m_a - o->m_b) / sqrt(o->m_a_se * o->m_a_se + o->m_b_se * o->m_b_se);
+    o->start_z = fmax(ze, zm);  // an undefined ratio (0/0) is skipped
+    for (int k = 0; k < 2; ++k) o->reserved[k] = 0.0;
   }
 }
 

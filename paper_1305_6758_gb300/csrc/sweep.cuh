@@ -66,16 +66,17 @@ struct Arith<float> {
     z = ct;
   }
   static __device__ __forceinline__ float add(float a, float b) { return a + b; }
-  static __device__ __forceinline__ float delta_e(float dx, float dy, float dz, float hx, float hy,
-                                                  float hz, float J, float hf) {
-    return -J * (dx * hx + dy * hy + dz * hz) - hf * dz;
-  }
-  // accept when dE <= 0, else iff u < exp(-beta dE) = 2^(-beta log2(e) dE);
-  // blog2e = beta log2(e) is precomputed per path.
-  static __device__ __forceinline__ bool accept(float dE, float blog2e, uint32_t r2) {
+  // Metropolis test of the move S -> S + d in the local field (hx, hy, hz):
+  // accept when dE <= 0, else iff u < exp(-beta dE) = 2^(-x), with
+  // x = beta log2(e) dE = (-b J) d.h_loc + (-b h) d_z and b = beta log2(e)
+  // precomputed per path (the two products are loop invariants).
+  static __device__ __forceinline__ bool accept_move(float dx, float dy, float dz, float hx,
+                                                     float hy, float hz, float J, float hf,
+                                                     float blog2e, uint32_t r2) {
+    const float x = fmaf(-blog2e * J, dx * hx + dy * hy + dz * hz, (-blog2e * hf) * dz);
     float p;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(p) : "f"(-blog2e * dE));
-    return dE <= 0.0f || uni(r2) < p;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(p) : "f"(-x));
+    return x <= 0.0f || uni(r2) < p;
   }
   static __device__ __forceinline__ float beta_param(double beta) {
     return static_cast<float>(beta * 1.4426950408889634);
@@ -121,7 +122,10 @@ struct Arith<double> {
     const double dot = __dadd_rn(__dadd_rn(__dmul_rn(dx, hx), __dmul_rn(dy, hy)), __dmul_rn(dz, hz));
     return __dsub_rn(__dmul_rn(-J, dot), __dmul_rn(hf, dz));
   }
-  static __device__ __forceinline__ bool accept(double dE, double beta, uint32_t r2) {
+  static __device__ __forceinline__ bool accept_move(double dx, double dy, double dz, double hx,
+                                                     double hy, double hz, double J, double hf,
+                                                     double beta, uint32_t r2) {
+    const double dE = delta_e(dx, dy, dz, hx, hy, hz, J, hf);
     return dE <= 0.0 || uni(r2) < exp(__dmul_rn(-beta, dE));
   }
   static __device__ __forceinline__ double beta_param(double beta) { return beta; }
@@ -213,9 +217,8 @@ __device__ __forceinline__ void update(uint32_t i, uint32_t sweep, uint32_t c2, 
   Real tx, ty, tz;
   A::trial(r.x, r.y, tx, ty, tz);
   const Real ax = own[hh], ay = own[S + hh], az = own[2 * S + hh];
-  const Real dE = A::delta_e(tx - ax, ty - ay, tz - az, hx, hy, hz, J, hf);
   Real nx = ax, ny = ay, nz = az;
-  if (A::accept(dE, bp, r.z)) {
+  if (A::accept_move(tx - ax, ty - ay, tz - az, hx, hy, hz, J, hf, bp, r.z)) {
     own[hh] = tx;
     own[S + hh] = ty;
     own[2 * S + hh] = tz;
@@ -285,6 +288,51 @@ __device__ __forceinline__ void half_sweep(const Geom& geo, int c, uint32_t swee
       const int oxp1 = (hx == HL - 1) ? -(HL - 1) : 1;  // +x offset when x is odd
       const int oxm0 = (hx == 0) ? (HL - 1) : -1;         // -x offset when x is even
       int z = t / LL;
+      using A = Arith<Real>;
+      if (dz == 1) {
+        // tp = HP: the thread walks planes z = 0 .. L-1 of its column, and
+        // the x parity of its site flips from plane to plane.  The other
+        // colour's spin at half index hh of plane z is then both an x
+        // neighbour of the site in plane z and the -z neighbour of the site
+        // in plane z + 1, and the +z neighbour of the site in plane z is an x
+        // neighbour of the site in plane z + 1: two of the six neighbours of
+        // every site after the first are already in registers.  The two x
+        // neighbours are added first in either order (a + b = b + a exactly),
+        // so the sum keeps the fixed order +x, -x, +y, -y, +z, -z.
+        Real ox = Real(0), oy = Real(0), oz = Real(0);  // half index hh, plane z
+        Real mzx = Real(0), mzy = Real(0), mzz = Real(0);  // -z neighbour
+#pragma unroll(kColumnUnroll<Real, LL>)
+        for (int hh = tid; hh < Geom::NH; hh += tp, ++z) {
+          const int p = (y + z + c) & 1;
+          if (hh == tid) {  // z = 0: the -z neighbour wraps to plane L - 1
+            const int n5 = hh + (LL - 1) * HP;
+            mzx = oth[n5];
+            mzy = oth[S + n5];
+            mzz = oth[2 * S + n5];
+            ox = oth[hh];
+            oy = oth[S + hh];
+            oz = oth[2 * S + hh];
+          }
+          const int nxo = hh + (p ? oxp1 : oxm0);
+          const int n2 = hh + oyp, n3 = hh + oym;
+          const int n4 = (z == LL - 1) ? hh - (LL - 1) * HP : hh + HP;
+          const Real czx = oth[n4], czy = oth[S + n4], czz = oth[2 * S + n4];
+          Real hx = A::add(A::add(A::add(A::add(A::add(ox, oth[nxo]), oth[n2]), oth[n3]), czx), mzx);
+          Real hy = A::add(A::add(A::add(A::add(A::add(oy, oth[S + nxo]), oth[S + n2]), oth[S + n3]),
+                                  czy), mzy);
+          Real hz = A::add(A::add(A::add(A::add(A::add(oz, oth[2 * S + nxo]), oth[2 * S + n2]),
+                                         oth[2 * S + n3]), czz), mzz);
+          update<Real, kMeas, kEnergy>(static_cast<uint32_t>(2 * hh + p), sweep, c2, c3, key, own, S,
+                                       hh, hx, hy, hz, J, hf, bp, accepted, part);
+          mzx = ox;
+          mzy = oy;
+          mzz = oz;
+          ox = czx;
+          oy = czy;
+          oz = czz;
+        }
+        return;
+      }
       // With dz = 2 the +z neighbour of one site of the column is the -z
       // neighbour of the next: it is loaded once.
       Real czx = Real(0), czy = Real(0), czz = Real(0);
@@ -308,7 +356,6 @@ __device__ __forceinline__ void half_sweep(const Geom& geo, int c, uint32_t swee
         czx = oth[n4];
         czy = oth[S + n4];
         czz = oth[2 * S + n4];
-        using A = Arith<Real>;
         Real hx = A::add(A::add(A::add(A::add(A::add(oth[n0], oth[n1]), oth[n2]), oth[n3]), czx), mzx);
         Real hy = A::add(A::add(A::add(A::add(A::add(oth[S + n0], oth[S + n1]), oth[S + n2]),
                                               oth[S + n3]), czy), mzy);
@@ -478,14 +525,15 @@ struct Meter {
 // or the ordered start of Sec. 5.
 template <typename Real>
 __device__ __forceinline__ void initial_spin(uint32_t i, uint32_t c2, uint32_t c3i,
-                                             const SweepParams& P, Real& x, Real& y, Real& z) {
+                                             const SweepParams& P, int mode, Real& x, Real& y,
+                                             Real& z) {
   using A = Arith<Real>;
   const Philox4 r = philox4x32_10(i, 0u, c2, c3i, P.key);
-  if (P.init_mode == MP_INIT_ORDERED) {
+  if (mode == MP_INIT_ORDERED) {
     x = Real(0);
     y = Real(0);
     z = Real(1);
-  } else if (P.init_mode == MP_INIT_ANGLES) {
+  } else if (mode == MP_INIT_ANGLES) {
     A::init_angles(r.x, r.y, x, y, z);
   } else {
     A::trial(r.x, r.y, x, y, z);
@@ -519,6 +567,7 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
   const uint32_t c2 = static_cast<uint32_t>(path);
   const uint32_t c3u = kTagUpdate | (static_cast<uint32_t>(sys_idx) << 8);
   const uint32_t c3i = kTagInit | (static_cast<uint32_t>(sys_idx) << 8);
+  const int init = path_init_mode(P.init_mode, path, sy.n_paths);
   const Real J = static_cast<Real>(sy.J), hf = static_cast<Real>(sy.h);
   const Real bp = A::beta_param(sy.beta);
   const bool columns = Geom::kColumns && (tp % Geom::HP) == 0;
@@ -529,7 +578,7 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
                           1.0 / static_cast<double>(sy.N), J, hf, j_first};
   unsigned char* st = path_state(P, sys_idx, path);
   Real* st_spins = st ? reinterpret_cast<Real*>(st + kStateHeader) : nullptr;
-  __shared__ int cancel_flag[16];
+  __shared__ int cancel_flag[kMaxGroups];
   const int gidx = bar - 1;
 
   if (P.resume && st) {  // continue from the saved state
@@ -544,7 +593,7 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
         int nn;
         const int i = geo.site(hh, c, nb, nn);
         Real x, y, z;
-        initial_spin<Real>(static_cast<uint32_t>(i), c2, c3i, P, x, y, z);
+        initial_spin<Real>(static_cast<uint32_t>(i), c2, c3i, P, init, x, y, z);
         own[hh] = x;
         own[S + hh] = y;
         own[2 * S + hh] = z;
@@ -720,6 +769,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
 // colour-1 update waits until the end (it needs colour 0 of plane L-1 new,
 // and colour 0 of plane L-1 needs colour 1 of plane 0 old).  Every update thus
 // sees exactly the neighbour values of the two-pass checkerboard sweep.
+// Phases (a) and (b) of a step run back to back, with one group barrier per
+// step (see the loop below for why no barrier is needed between them).
 // Ring indices: colour-0 step index q' = 0..L+1 (planes 0..L-1, 0, 1) in slot
 // q' mod 4; colour-1 step index q' = -1..L (planes L-1, 0..L-1, 0) in slot
 // (q'+1) mod 5.  Every load is issued two steps before its first use.
@@ -759,6 +810,7 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
   const uint32_t c2 = static_cast<uint32_t>(path);
   const uint32_t c3u = kTagUpdate | (static_cast<uint32_t>(sys_idx) << 8);
   const uint32_t c3i = kTagInit | (static_cast<uint32_t>(sys_idx) << 8);
+  const int init = path_init_mode(P.init_mode, path, sy.n_paths);
   const Real J = static_cast<Real>(sy.J), hf = static_cast<Real>(sy.h);
   const Real bp = A::beta_param(sy.beta);
   const int64_t j_first = P.s_begin > P.n_therm ? P.s_begin - P.n_therm : 0;
@@ -766,7 +818,7 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
                           reinterpret_cast<Real*>(slice + slice_red_offset()),
                           sy.ring, tp >> 5, tid & 31, tid >> 5, tid,
                           1.0 / static_cast<double>(sy.N), J, hf, j_first};
-  __shared__ int abort_flag[16];  // per thread group: a bounded wait gave up, or canceled
+  __shared__ int abort_flag[kMaxGroups];  // per thread group: a bounded wait gave up, or canceled
   const int gidx = bar - 1;
   const bool producer = tid == 0;
   const bool resume = P.resume && st;
@@ -778,7 +830,7 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
     const int x = i % L, y = (i / L) % L, z = i / (L * L);
     const int c = (x + y + z) & 1;
     Real sx, sy_, sz;
-    initial_spin<Real>(static_cast<uint32_t>(i), c2, c3i, P, sx, sy_, sz);
+    initial_spin<Real>(static_cast<uint32_t>(i), c2, c3i, P, init, sx, sy_, sz);
     Real* hpl = plane(z, c);
     const int hp = (x >> 1) + HL * y;
     hpl[hp] = sx;
@@ -888,8 +940,15 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
         }
       }
     };
+    // One barrier per step.  A thread updates the same half indices hp in
+    // both phases, and the colour-1 site at (hp, plane q-1) has the colour-0
+    // site at (hp, plane q) as its +z neighbour: phase (b) reads the thread's
+    // own results of phase (a), and every other value either phase reads was
+    // written before the previous barrier (in-plane neighbours of the other
+    // colour come from the previous step) or is written after the next one.
     for (int q = 0; q <= L + 1; ++q) {
       if (q < L) phase(0, q, c0buf(q), c1buf(q), c1buf(q + 1), c1buf(q - 1), false);
+      if (q >= 2) phase(1, wrap(q - 1), c1buf(q - 1), c0buf(q - 1), c0buf(q), c0buf(q - 2), meas);
       fence_async_shared();
       // the buffers step q+1 starts with were issued at step q-1: the producer
       // confirms them now, and the barrier below hands them to every thread
@@ -900,15 +959,13 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
         break;
       }
       if (meas && q == 0) meter.maybe_flush(j);
-      if (producer && q < L) tma_store(plane(q, 0), c0buf(q), bytes);
-      if (q >= 2) phase(1, wrap(q - 1), c1buf(q - 1), c0buf(q - 1), c0buf(q), c0buf(q - 2), meas);
-      fence_async_shared();
-      group_sync(tp, bar);
       if (producer) {  // after the barrier: the buffers just written are complete
+        if (q < L) tma_store(plane(q, 0), c0buf(q), bytes);
         if (q >= 2) tma_store(plane(wrap(q - 1), 1), c1buf(q - 1), bytes);
-        // the slots refilled now last held colour-0 index q-2 (stored at step
-        // q-2) and colour-1 index q-2 (stored at step q-1): all but the two
-        // newest store groups must have finished reading shared memory
+        // the slots refilled now last held colour-0 index q-2 (stored after
+        // step q-2) and colour-1 index q-2 (stored after step q-1): all but
+        // this step's (at most two) store groups must have finished reading
+        // shared memory
         tma_wait_read(2);
         // colour-0 step indices L and L+1 reload planes 0 and 1 written this sweep
         if (q + 2 >= L) tma_wait_all();

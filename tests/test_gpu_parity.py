@@ -225,3 +225,40 @@ def test_rerun_and_seed():
         c = sim.paths(0)
     assert np.array_equal(a, b)
     assert not np.array_equal(a, c)
+
+
+# ----------------------------------------------------- thread layouts -------
+@pytest.mark.parametrize("L,tp", [
+    (8, 32),    # threads per path = sites per z-plane of one colour: column walk, step 1
+    (8, 64),    # step 2
+    (8, 96),    # step 3
+    (8, 128),   # step 4
+    (8, 160),   # not a multiple of a plane: every site decoded from its index
+    (12, 72 * 4),
+    (16, 128),
+    (16, 256),
+])
+def test_fp64_every_walk_layout_matches_oracle(L, tp):
+    """Each thread-to-site layout of the shared-memory sweep (the column walk
+    that reuses z and x neighbours across planes, and the generic decode)
+    gives the oracle's per-path records."""
+    systems = [mp.System(L, 1.1, h=0.03, n_paths=5)]
+    recs, _, _ = run_gpu(systems, 2, 3, seed=8, precision=mp.FP64, threads_per_path=tp)
+    ref = O.run([osys(systems[0])], 2, 3, seed=8)[0]
+    np.testing.assert_allclose(recs[0][:, RECORD_FIELDS], ref[:, RECORD_FIELDS], rtol=1e-10, atol=1e-13)
+    np.testing.assert_array_equal(recs[0][:, 17], ref[:, 17])
+    with mp.Simulation(systems, 1, 1, precision=mp.FP64, threads_per_path=tp) as sim:
+        assert sim.system_plan(0)["threads_per_path"] == tp
+
+
+def test_fp32_trajectories_do_not_depend_on_the_layout():
+    """FP32, L=16: column walks with step 1, 2 and 4 planes and paths of one
+    warp give the same records (the same arithmetic per site in the same order)."""
+    systems = [mp.System(16, 1.3, n_paths=6)]
+    base = None
+    for tp in (128, 256, 512, 96):
+        recs, _, _ = run_gpu(systems, 3, 5, seed=9, threads_per_path=tp)
+        if base is None:
+            base = recs[0]
+        else:
+            np.testing.assert_allclose(recs[0][:, RECORD_FIELDS], base[:, RECORD_FIELDS], rtol=2e-6, atol=2e-7)

@@ -236,6 +236,39 @@ def test_random_site_order_agrees_with_checkerboard():
         assert zdiff(a[k], b[k], np.hypot(a[k + "_se"], b[k + "_se"])) < 4
 
 
+def test_random_site_order_draws_sites_uniformly():
+    """At infinite temperature every move is accepted, so after one sweep of N
+    random sites exactly the never-drawn sites keep their initial spin: a
+    fraction (1 - 1/N)^N ~ 1/e for uniform draws."""
+    L, N, P = 16, 4096, 8
+    _, sp = O.run([O.System(L=L, T=1e300, n_paths=P)], 0, 1, order_mode=O.ORDER_RANDOM, want_spins=True)
+    kept = 0
+    for p in range(P):
+        s0 = O.init(O.SC, L, p, 0, 1, O.INIT_SPHERE)
+        kept += int(np.sum(np.all(sp[0][p] == s0, axis=1)))
+    frac = kept / (N * P)
+    expect = (1 - 1 / N) ** N
+    assert abs(frac - expect) < 4 * np.sqrt(expect * (1 - expect) / (N * P))
+
+
+def test_two_start_split_and_convergence():
+    """Sec. 4's check: half the paths from the random state, half from the
+    ordered state.  The split is exact (each half equals the matching
+    single-start run path by path); the halves disagree after one sweep and
+    agree once thermalised."""
+    s = [O.System(L=4, T=1.0, n_paths=65)]
+    two = O.run(s, 0, 1, two_start=True)[0]
+    rnd = O.run(s, 0, 1)[0]
+    ordd = O.run(s, 0, 1, init_mode=O.INIT_ORDERED)[0]
+    np.testing.assert_array_equal(two[:33], rnd[:33])
+    np.testing.assert_array_equal(two[33:], ordd[33:])
+    early = O.estimates(two, 64, 1.0)
+    assert early["e_b"] < early["e_a"] and early["start_z"] > 10
+    late = O.estimates(O.run([O.System(L=4, T=1.0, n_paths=512)], 400, 400, two_start=True)[0], 64, 1.0)
+    assert late["start_z"] < 4
+    assert np.isclose(late["e_a"] * 256 + late["e_b"] * 256, late["e"] * 512)
+
+
 def _r_critical(n, alpha=1e-3, reps=4000):
     """Lower alpha-quantile of the distribution coefficient for normal samples of size n."""
     rng = np.random.default_rng(2024)
