@@ -69,7 +69,7 @@ int64_t sites_of(const mp_system& s) {
 int64_t lattice_bytes(const mp_system& s, int real) {
   const int64_t NH = (sites_of(s) + 1) / 2;
   if (s.lattice == MP_LATTICE_ISING) return kIsingThrBytes + 2 * NH;
-  return 6 * NH * real;
+  return 6 * ((NH + 1) & ~int64_t{1}) * real;  // per colour: (x, y) pairs then z, even length
 }
 
 // Ising acceptance as an integer test on a Philox word r (Appendix A kernel):
@@ -959,6 +959,9 @@ int ensure_state(mp_state* h) {
   return MP_OK;
 }
 
+// Version 2: spins stored as (x, y) pairs then z per colour (or half-plane).
+constexpr uint64_t kCheckpointVersion = 2;
+
 struct CheckpointHeader {
   char magic[8];
   uint64_t version;
@@ -1038,7 +1041,7 @@ int mp_checkpoint(mp_handle h, void* buf, size_t* nbytes) {
   DeviceGuard dg(h->device);
   CheckpointHeader hd{};
   std::memcpy(hd.magic, "MPCKPT01", 8);
-  hd.version = 1;
+  hd.version = kCheckpointVersion;
   hd.config_hash = config_hash(h);
   hd.sweeps_done = h->sweeps_done;
   hd.state_bytes = h->state_bytes;
@@ -1056,7 +1059,7 @@ int mp_restore(mp_handle h, const void* buf, size_t nbytes) {
   if (nbytes < sizeof(CheckpointHeader)) return fail(h, MP_EINVAL, "checkpoint too short");
   CheckpointHeader hd;
   std::memcpy(&hd, buf, sizeof(hd));
-  if (std::memcmp(hd.magic, "MPCKPT01", 8) != 0 || hd.version != 1)
+  if (std::memcmp(hd.magic, "MPCKPT01", 8) != 0 || hd.version != kCheckpointVersion)
     return fail(h, MP_EINVAL, "not a checkpoint of this library");
   if (hd.config_hash != config_hash(h))
     return fail(h, MP_EINVAL, "checkpoint of a different configuration");

@@ -109,7 +109,7 @@ extern "C" int mp_run_noalloc(const mp_system* systems, int n_systems, int preci
     const int N = s.lattice == MP_LATTICE_SC ? s.L * s.L * s.L : s.L;
     const int NH = (N + 1) / 2;
     const int tp = std::min(cta_max, std::max(32, round_up((NH + 7) / 8, 32)));
-    const int slice = round_up(mpk::slice_spin_offset(tp, 1) + 6 * NH * real, 128);
+    const int slice = round_up(mpk::slice_spin_offset(tp, 1) + 6 * round_up(NH, 2) * real, 128);
     if (slice > smem_max) return MP_EINVAL;
     DevSystem& ds = g_systems[k];
     std::memset(&ds, 0, sizeof(ds));

@@ -18,9 +18,10 @@
 // The colour-1 pass sees final colour-0 neighbours, so the sum over colour-1
 // sites of S_i . h_loc,i visits every bond once: the energy comes for free.
 //
-// Shared-memory layout of one path: [colour][component][half index], the half
-// index of site i = x + L(y + Lz) being i >> 1, so a warp's 32 consecutive
-// sites of one colour and their +-y, +-z neighbours are 32 consecutive words.
+// Shared-memory layout of one path: [colour][(x, y) pairs | z][half index],
+// the half index of site i = x + L(y + Lz) being i >> 1, so a spin is one
+// 8-byte and one 4-byte load (16 + 8 in FP64) and a warp's 32 consecutive
+// sites of one colour and their +-y, +-z neighbours are consecutive elements.
 #pragma once
 #include <cstdint>
 
@@ -175,7 +176,8 @@ struct GeomChain {
   static constexpr bool kColumns = false;
   static constexpr int HP = 1;
   __device__ __forceinline__ int count(int c) const { return c == 0 ? (N + 1) >> 1 : N >> 1; }
-  __device__ __forceinline__ int stride() const { return (N + 1) >> 1; }
+  // even, so that every (x, y) pair array starts on a pair boundary
+  __device__ __forceinline__ int stride() const { return (((N + 1) >> 1) + 1) & ~1; }
   __device__ __forceinline__ int site(int h, int c, int* nb, int& nn) const {
     const int i = 2 * h + c;
     nn = 0;
@@ -203,25 +205,66 @@ struct Partials {
   Real eb, mx, my, mz;
 };
 
-// The Metropolis step at site i (half index hh of the colour array `own`,
-// component stride S) given its local field (hx, hy, hz), Sec. 2.2: trial
-// spin, energy change from the local field, acceptance test.
+// ------------------------------------------------------------ spin views --
+template <typename Real>
+struct V3 {
+  Real x, y, z;
+};
+template <typename Real>
+__device__ __forceinline__ V3<Real> add3(V3<Real> a, V3<Real> b) {
+  using A = Arith<Real>;
+  return V3<Real>{A::add(a.x, b.x), A::add(a.y, b.y), A::add(a.z, b.z)};
+}
+template <typename Real>
+struct PairOf;
+template <>
+struct PairOf<float> {
+  using T = float2;
+};
+template <>
+struct PairOf<double> {
+  using T = double2;
+};
+
+// S spins of one colour (or one half-plane): their (x, y) pairs, then their z
+// components.  base must be aligned to a pair and S even.
+template <typename Real>
+struct SpinView {
+  using P2 = typename PairOf<Real>::T;
+  P2* xy;
+  Real* z;
+  __device__ __forceinline__ SpinView(Real* base, int S)
+      : xy(reinterpret_cast<P2*>(base)), z(base + 2 * S) {}
+  __device__ __forceinline__ V3<Real> ld(int h) const {
+    const P2 v = xy[h];
+    return V3<Real>{v.x, v.y, z[h]};
+  }
+  __device__ __forceinline__ void st(int h, Real a, Real b, Real c) const {
+    P2 v;
+    v.x = a;
+    v.y = b;
+    xy[h] = v;
+    z[h] = c;
+  }
+};
+
+// The Metropolis step at site i (half index hh of the colour view `own`)
+// given its local field (hx, hy, hz), Sec. 2.2: trial spin, energy change
+// from the local field, acceptance test.
 template <typename Real, bool kMeas, bool kEnergy>
 __device__ __forceinline__ void update(uint32_t i, uint32_t sweep, uint32_t c2, uint32_t c3,
-                                       const PhiloxKeys& key, Real* __restrict__ own, int S, int hh,
-                                       Real hx,
-                                       Real hy, Real hz, Real J, Real hf, Real bp, int& accepted,
-                                       Partials<Real>& part) {
+                                       const PhiloxKeys& key, const SpinView<Real>& own, int hh,
+                                       Real hx, Real hy, Real hz, Real J, Real hf, Real bp,
+                                       int& accepted, Partials<Real>& part) {
   using A = Arith<Real>;
   const Philox4 r = philox4x32_10(i, sweep, c2, c3, key);
   Real tx, ty, tz;
   A::trial(r.x, r.y, tx, ty, tz);
-  const Real ax = own[hh], ay = own[S + hh], az = own[2 * S + hh];
+  const V3<Real> a = own.ld(hh);
+  const Real ax = a.x, ay = a.y, az = a.z;
   Real nx = ax, ny = ay, nz = az;
   if (A::accept_move(tx - ax, ty - ay, tz - az, hx, hy, hz, J, hf, bp, r.z)) {
-    own[hh] = tx;
-    own[S + hh] = ty;
-    own[2 * S + hh] = tz;
+    own.st(hh, tx, ty, tz);
     nx = tx;
     ny = ty;
     nz = tz;
@@ -239,28 +282,24 @@ __device__ __forceinline__ void update(uint32_t i, uint32_t sweep, uint32_t c2, 
 // summed in the fixed order nb[0], nb[1], ...
 template <typename Real, int NNB, bool kMeas, bool kEnergy>
 __device__ __forceinline__ void attempt(uint32_t i, uint32_t sweep, uint32_t c2, uint32_t c3,
-                                        const PhiloxKeys& key, Real* own, const Real* oth, int S,
-                                        int hh, const int* nb, int nn, Real J, Real hf, Real bp,
-                                        int& accepted, Partials<Real>& part) {
-  using A = Arith<Real>;
-  Real hx = Real(0), hy = Real(0), hz = Real(0);
+                                        const PhiloxKeys& key, const SpinView<Real>& own,
+                                        const SpinView<Real>& oth, int hh, const int* nb, int nn,
+                                        Real J, Real hf, Real bp, int& accepted,
+                                        Partials<Real>& part) {
+  V3<Real> f{Real(0), Real(0), Real(0)};
 #pragma unroll
   for (int j = 0; j < NNB; ++j) {
-    if (j < nn) {
-      hx = A::add(hx, oth[nb[j]]);
-      hy = A::add(hy, oth[S + nb[j]]);
-      hz = A::add(hz, oth[2 * S + nb[j]]);
-    }
+    if (j < nn) f = add3(f, oth.ld(nb[j]));
   }
-  update<Real, kMeas, kEnergy>(i, sweep, c2, c3, key, own, S, hh, hx, hy, hz, J, hf, bp, accepted,
+  update<Real, kMeas, kEnergy>(i, sweep, c2, c3, key, own, hh, f.x, f.y, f.z, J, hf, bp, accepted,
                                part);
 }
 
 // Sites of a column interleaved by the compiler (independent Philox chains):
-// 4 in the FP32 kernels with 128 registers per thread (L <= 16), 2 in those
-// with 64.
+// 4 in the FP32 kernels with 128 registers per thread (L <= 16); none in
+// those with 64, where unrolling spills registers.
 template <typename Real, int L>
-constexpr int kColumnUnroll = sizeof(Real) == 8 ? 1 : (L <= 16 ? 4 : 2);
+constexpr int kColumnUnroll = sizeof(Real) == 8 ? 1 : (L <= 16 ? 4 : 1);
 
 // One half-sweep of one thread: every site of colour c it owns.
 //
@@ -274,8 +313,8 @@ __device__ __forceinline__ void half_sweep(const Geom& geo, int c, uint32_t swee
                                            int tp, bool columns, Real J, Real hf, Real bp,
                                            int& accepted, Partials<Real>& part) {
   const int S = geo.stride();
-  Real* own = sp + c * 3 * S;
-  const Real* oth = sp + (1 - c) * 3 * S;
+  const SpinView<Real> own(sp + c * 3 * S, S);
+  const SpinView<Real> oth(sp + (1 - c) * 3 * S, S);
   if constexpr (Geom::kColumns) {
     if (columns) {
       constexpr int HL = Geom::HL, HP = Geom::HP, LL = 2 * Geom::HL;
@@ -299,70 +338,46 @@ __device__ __forceinline__ void half_sweep(const Geom& geo, int c, uint32_t swee
         // every site after the first are already in registers.  The two x
         // neighbours are added first in either order (a + b = b + a exactly),
         // so the sum keeps the fixed order +x, -x, +y, -y, +z, -z.
-        Real ox = Real(0), oy = Real(0), oz = Real(0);  // half index hh, plane z
-        Real mzx = Real(0), mzy = Real(0), mzz = Real(0);  // -z neighbour
+        V3<Real> o0{Real(0), Real(0), Real(0)};  // half index hh, plane z
+        V3<Real> mz{Real(0), Real(0), Real(0)};  // -z neighbour
 #pragma unroll(kColumnUnroll<Real, LL>)
         for (int hh = tid; hh < Geom::NH; hh += tp, ++z) {
           const int p = (y + z + c) & 1;
           if (hh == tid) {  // z = 0: the -z neighbour wraps to plane L - 1
-            const int n5 = hh + (LL - 1) * HP;
-            mzx = oth[n5];
-            mzy = oth[S + n5];
-            mzz = oth[2 * S + n5];
-            ox = oth[hh];
-            oy = oth[S + hh];
-            oz = oth[2 * S + hh];
+            mz = oth.ld(hh + (LL - 1) * HP);
+            o0 = oth.ld(hh);
           }
           const int nxo = hh + (p ? oxp1 : oxm0);
-          const int n2 = hh + oyp, n3 = hh + oym;
           const int n4 = (z == LL - 1) ? hh - (LL - 1) * HP : hh + HP;
-          const Real czx = oth[n4], czy = oth[S + n4], czz = oth[2 * S + n4];
-          Real hx = A::add(A::add(A::add(A::add(A::add(ox, oth[nxo]), oth[n2]), oth[n3]), czx), mzx);
-          Real hy = A::add(A::add(A::add(A::add(A::add(oy, oth[S + nxo]), oth[S + n2]), oth[S + n3]),
-                                  czy), mzy);
-          Real hz = A::add(A::add(A::add(A::add(A::add(oz, oth[2 * S + nxo]), oth[2 * S + n2]),
-                                         oth[2 * S + n3]), czz), mzz);
-          update<Real, kMeas, kEnergy>(static_cast<uint32_t>(2 * hh + p), sweep, c2, c3, key, own, S,
-                                       hh, hx, hy, hz, J, hf, bp, accepted, part);
-          mzx = ox;
-          mzy = oy;
-          mzz = oz;
-          ox = czx;
-          oy = czy;
-          oz = czz;
+          const V3<Real> cz = oth.ld(n4);
+          const V3<Real> f =
+              add3(add3(add3(add3(add3(o0, oth.ld(nxo)), oth.ld(hh + oyp)), oth.ld(hh + oym)), cz), mz);
+          update<Real, kMeas, kEnergy>(static_cast<uint32_t>(2 * hh + p), sweep, c2, c3, key, own, hh,
+                                       f.x, f.y, f.z, J, hf, bp, accepted, part);
+          mz = o0;
+          o0 = cz;
         }
         return;
       }
       // With dz = 2 the +z neighbour of one site of the column is the -z
       // neighbour of the next: it is loaded once.
-      Real czx = Real(0), czy = Real(0), czz = Real(0);
+      V3<Real> cz{Real(0), Real(0), Real(0)};
 #pragma unroll(kColumnUnroll<Real, LL>)
       for (int hh = tid; hh < Geom::NH; hh += tp, z += dz) {
         const int p = (y + z + c) & 1;
         const int n0 = hh + (p ? oxp1 : 0), n1 = hh + (p ? 0 : oxm0);
-        const int n2 = hh + oyp, n3 = hh + oym;
         const int n4 = (z == LL - 1) ? hh - (LL - 1) * HP : hh + HP;
-        Real mzx, mzy, mzz;
+        V3<Real> mz;
         if (dz == 2 && hh != tid) {
-          mzx = czx;
-          mzy = czy;
-          mzz = czz;
+          mz = cz;
         } else {
-          const int n5 = (z == 0) ? hh + (LL - 1) * HP : hh - HP;
-          mzx = oth[n5];
-          mzy = oth[S + n5];
-          mzz = oth[2 * S + n5];
+          mz = oth.ld((z == 0) ? hh + (LL - 1) * HP : hh - HP);
         }
-        czx = oth[n4];
-        czy = oth[S + n4];
-        czz = oth[2 * S + n4];
-        Real hx = A::add(A::add(A::add(A::add(A::add(oth[n0], oth[n1]), oth[n2]), oth[n3]), czx), mzx);
-        Real hy = A::add(A::add(A::add(A::add(A::add(oth[S + n0], oth[S + n1]), oth[S + n2]),
-                                              oth[S + n3]), czy), mzy);
-        Real hz = A::add(A::add(A::add(A::add(A::add(oth[2 * S + n0], oth[2 * S + n1]),
-                                                     oth[2 * S + n2]), oth[2 * S + n3]), czz), mzz);
-        update<Real, kMeas, kEnergy>(static_cast<uint32_t>(2 * hh + p), sweep, c2, c3, key, own, S,
-                                     hh, hx, hy, hz, J, hf, bp, accepted, part);
+        cz = oth.ld(n4);
+        const V3<Real> f = add3(
+            add3(add3(add3(add3(oth.ld(n0), oth.ld(n1)), oth.ld(hh + oyp)), oth.ld(hh + oym)), cz), mz);
+        update<Real, kMeas, kEnergy>(static_cast<uint32_t>(2 * hh + p), sweep, c2, c3, key, own, hh,
+                                     f.x, f.y, f.z, J, hf, bp, accepted, part);
       }
       return;
     }
@@ -373,7 +388,7 @@ __device__ __forceinline__ void half_sweep(const Geom& geo, int c, uint32_t swee
     int nn;
     const int i = geo.site(hh, c, nb, nn);
     attempt<Real, Geom::NNB, kMeas, kEnergy>(static_cast<uint32_t>(i), sweep, c2, c3, key, own, oth,
-                                             S, hh, nb, nn, J, hf, bp, accepted, part);
+                                             hh, nb, nn, J, hf, bp, accepted, part);
   }
 }
 
@@ -586,7 +601,7 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
     if (tid < kAccDoubles) meter.acc[tid] = reinterpret_cast<const double*>(st)[tid];
   } else {
     for (int c = 0; c < 2; ++c) {
-      Real* own = sp + c * 3 * S;
+      const SpinView<Real> own(sp + c * 3 * S, S);
       const int cnt = geo.count(c);
       for (int hh = tid; hh < cnt; hh += tp) {
         int nb[Geom::NNB];
@@ -594,9 +609,7 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
         const int i = geo.site(hh, c, nb, nn);
         Real x, y, z;
         initial_spin<Real>(static_cast<uint32_t>(i), c2, c3i, P, init, x, y, z);
-        own[hh] = x;
-        own[S + hh] = y;
-        own[2 * S + hh] = z;
+        own.st(hh, x, y, z);
       }
     }
     if (tid < kAccDoubles) meter.acc[tid] = 0.0;
@@ -651,10 +664,10 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
 
   Real worst = Real(0);
   for (int c = 0; c < 2; ++c) {
-    const Real* own = sp + c * 3 * S;
+    const SpinView<Real> own(sp + c * 3 * S, S);
     for (int hh = tid; hh < geo.count(c); hh += tp) {
-      const Real x = own[hh], y = own[S + hh], z = own[2 * S + hh];
-      worst = fmax(worst, fabs(sqrt(x * x + y * y + z * z) - Real(1)));
+      const V3<Real> v = own.ld(hh);
+      worst = fmax(worst, fabs(sqrt(v.x * v.x + v.y * v.y + v.z * v.z) - Real(1)));
     }
   }
   if (P.save && st) {
@@ -667,14 +680,15 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
   if (P.spins != nullptr) {
     double* out = P.spins + P.spin_offset[sys_idx] + path * 3 * static_cast<int64_t>(sy.N);
     for (int c = 0; c < 2; ++c) {
-      const Real* own = sp + c * 3 * S;
+      const SpinView<Real> own(sp + c * 3 * S, S);
       for (int hh = tid; hh < geo.count(c); hh += tp) {
         int nb[Geom::NNB];
         int nn;
         const int i = geo.site(hh, c, nb, nn);
-        out[3 * i + 0] = own[hh];
-        out[3 * i + 1] = own[S + hh];
-        out[3 * i + 2] = own[2 * S + hh];
+        const V3<Real> v = own.ld(hh);
+        out[3 * i + 0] = v.x;
+        out[3 * i + 1] = v.y;
+        out[3 * i + 2] = v.z;
       }
     }
   }
@@ -757,8 +771,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
 
 // ---------------------------------------------------- streamed from HBM --
 // Lattices too large for shared memory.  Each path's spins stay in HBM in the
-// layout [z][colour][component][L*L/2] (a "half-plane" is one colour of one
-// z-plane, padded to 16 bytes), in a buffer owned by the thread group for the
+// layout [z][colour][(x, y) pairs | z][L*L/2] (a "half-plane" is one colour
+// of one z-plane, padded to 16 bytes), in a buffer owned by the thread group for the
 // whole run.  A sweep walks the z-planes as a wavefront over a ring of 4 + 5
 // half-plane buffers in shared memory, filled by TMA bulk copies and written
 // back by bulk stores:
@@ -833,9 +847,7 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
     initial_spin<Real>(static_cast<uint32_t>(i), c2, c3i, P, init, sx, sy_, sz);
     Real* hpl = plane(z, c);
     const int hp = (x >> 1) + HL * y;
-    hpl[hp] = sx;
-    hpl[HP + hp] = sy_;
-    hpl[2 * HP + hp] = sz;
+    SpinView<Real>(hpl, HP).st(hp, sx, sy_, sz);
   }
   fence_async_global();
   if (tid < kAccDoubles) meter.acc[tid] = resume ? reinterpret_cast<const double*>(st)[tid] : 0.0;
@@ -909,8 +921,9 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
     // are too (oxp1: +x when x is odd, oxm0: -x when x is even).
     const int oxp1 = (hx == HL - 1) ? -(HL - 1) : 1;
     const int oxm0 = (hx == 0) ? (HL - 1) : -1;
-    auto phase = [&](int c, int z, Real* __restrict__ own, const Real* __restrict__ same,
-                     const Real* __restrict__ up, const Real* __restrict__ dn, bool energy) {
+    auto phase = [&](int c, int z, Real* own_base, Real* same_base, Real* up_base, Real* dn_base,
+                     bool energy) {
+      const SpinView<Real> own(own_base, HP), same(same_base, HP), up(up_base, HP), dn(dn_base, HP);
 #pragma unroll 4
       for (int y = y0; y < L; y += RS) {
         const int hp = hx + HL * y;
@@ -919,23 +932,18 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
         const int xm = hp + (p ? 0 : oxm0);
         const int yp = (y == L - 1) ? hp - (L - 1) * HL : hp + HL;
         const int ym = (y == 0) ? hp + (L - 1) * HL : hp - HL;
-        Real f[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const int o = k * HP;
-          f[k] = A::add(A::add(A::add(A::add(A::add(same[o + xp], same[o + xm]), same[o + yp]),
-                                       same[o + ym]), up[o + hp]), dn[o + hp]);
-        }
+        const V3<Real> f = add3(add3(add3(add3(add3(same.ld(xp), same.ld(xm)), same.ld(yp)), same.ld(ym)),
+                                     up.ld(hp)), dn.ld(hp));
         const uint32_t i = static_cast<uint32_t>(2 * (hp + HP * z) + p);
         if (meas) {
           if (energy)
-            update<Real, true, true>(i, sw, c2, c3u, P.key, own, HP, hp, f[0], f[1], f[2], J, hf, bp,
+            update<Real, true, true>(i, sw, c2, c3u, P.key, own, hp, f.x, f.y, f.z, J, hf, bp,
                                      accepted, part);
           else
-            update<Real, true, false>(i, sw, c2, c3u, P.key, own, HP, hp, f[0], f[1], f[2], J, hf,
-                                      bp, accepted, part);
+            update<Real, true, false>(i, sw, c2, c3u, P.key, own, hp, f.x, f.y, f.z, J, hf, bp,
+                                      accepted, part);
         } else {
-          update<Real, false, false>(i, sw, c2, c3u, P.key, own, HP, hp, f[0], f[1], f[2], J, hf, bp,
+          update<Real, false, false>(i, sw, c2, c3u, P.key, own, hp, f.x, f.y, f.z, J, hf, bp,
                                      accepted, part);
         }
       }
@@ -1000,9 +1008,9 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
   Real worst = Real(0);  // in the working precision: FP64 runs at 1/64 rate on this GPU
   for (int i = tid; i < N; i += tp) {
     const int x = i % L, y = (i / L) % L, z = i / (L * L);
-    const Real* hpl = plane(z, (x + y + z) & 1);
     const int hp = (x >> 1) + HL * y;
-    const Real a = hpl[hp], b = hpl[HP + hp], c = hpl[2 * HP + hp];
+    const V3<Real> v = SpinView<Real>(plane(z, (x + y + z) & 1), HP).ld(hp);
+    const Real a = v.x, b = v.y, c = v.z;
     worst = fmax(worst, fabs(sqrt(a * a + b * b + c * c) - Real(1)));
     if (P.spins != nullptr) {
       double* out = P.spins + P.spin_offset[sys_idx] + path * 3 * static_cast<int64_t>(N);
