@@ -35,6 +35,10 @@ cudaError_t sweep_occupancy(int precision, int variant, int cta, int smem, int* 
 cudaError_t launch_sweep(int precision, int variant, const SweepParams& p, int grid, int cta,
                          int smem, cudaStream_t st);
 
+// The streamed kernel compiled for simple cubic L = 64 (all systems of the
+// batch streamed at that size).
+constexpr int kStreamL64 = -1064;
+
 // The square-lattice Ising kernel (variant kIsingKernel), any even L.
 constexpr int kIsingKernel = -3;
 cudaError_t ising_prepare(int device, int* max_dynamic, int* max_threads);

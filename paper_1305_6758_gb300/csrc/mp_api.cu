@@ -298,11 +298,17 @@ int plan(mp_state* h, const mp_config* cfg) {
   auto variant_of = [&](const mp_system& sy) {
     if (sy.lattice == MP_LATTICE_ISING) return kIsingKernel;
     if (sy.lattice == MP_LATTICE_CHAIN) return -1;
-    return streamed(sy, h->precision, h->flags) ? -2 : sy.L;
+    if (!streamed(sy, h->precision, h->flags)) return sy.L;
+    return sy.L == 64 ? kStreamL64 : -2;  // L = 64 has a kernel compiled for its size
   };
   int variant = variant_of(h->systems[0]);
-  for (int k = 1; k < n; ++k)
-    if (variant_of(h->systems[k]) != variant) variant = 0;
+  bool all_streamed = true;
+  for (int k = 0; k < n; ++k) {
+    const int v = variant_of(h->systems[k]);
+    all_streamed = all_streamed && (v == -2 || v == kStreamL64);
+    if (v != variant) variant = 0;
+  }
+  if (variant == 0 && all_streamed) variant = -2;  // streamed sizes mixed: one streamed kernel
   h->variant = variant;
   int sms = 0, smem_max = 0, cta_max = 0;
   MP_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));

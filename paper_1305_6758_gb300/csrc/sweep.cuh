@@ -798,12 +798,16 @@ struct StreamLayout {
   }
 };
 
-template <typename Real>
+// kL > 0: the lattice size is the compile-time constant kL, which turns the
+// in-plane index arithmetic and the buffer offsets into immediates; kL = 0:
+// any even L (sy.L).  kRS > 0: tp = kRS * L/2 threads per path, so every
+// thread owns exactly kL / kRS rows at compile-time offsets.
+template <typename Real, int kL, int kRS>
 __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path,
                                   const SweepParams& P, unsigned char* slice, int tid, int tp,
                                   int bar, Real* lat_cta) {
   using A = Arith<Real>;
-  const int L = sy.L, HL = L / 2, HP = L * L / 2;
+  const int L = kL > 0 ? kL : sy.L, HL = L / 2, HP = L * L / 2;
   const int hps = StreamLayout<Real>::hps(L);
   const uint32_t bytes = static_cast<uint32_t>(hps * sizeof(Real));
   // [9 mbarriers][9 load counters] in 128 bytes, then the 9 half-plane buffers
@@ -866,7 +870,8 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
   group_sync(tp, bar);
 
   // In-plane thread layout: column hx, rows y0, y0 + RS, ...
-  const int RS = tp / HL;
+  const int RS = kRS > 0 ? kRS : tp / HL;
+  constexpr bool kFixedRows = kL > 0 && kRS > 0 && kL % kRS == 0;
   const bool active = tid < HL * RS;
   const int hx = active ? tid % HL : 0;
   const int y0 = active ? tid / HL : L;
@@ -924,8 +929,7 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
     auto phase = [&](int c, int z, Real* own_base, Real* same_base, Real* up_base, Real* dn_base,
                      bool energy) {
       const SpinView<Real> own(own_base, HP), same(same_base, HP), up(up_base, HP), dn(dn_base, HP);
-#pragma unroll 4
-      for (int y = y0; y < L; y += RS) {
+      auto row = [&](int y) {
         const int hp = hx + HL * y;
         const int p = (y + z + c) & 1;
         const int xp = hp + (p ? oxp1 : 0);
@@ -946,6 +950,15 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
           update<Real, false, false>(i, sw, c2, c3u, P.key, own, hp, f.x, f.y, f.z, J, hf, bp,
                                      accepted, part);
         }
+      };
+      if constexpr (kFixedRows) {
+        if (active) {
+#pragma unroll
+          for (int k = 0; k < kL / kRS; ++k) row(y0 + k * kRS);
+        }
+      } else {
+#pragma unroll 4
+        for (int y = y0; y < L; y += RS) row(y);
       }
     };
     // One barrier per step.  A thread updates the same half indices hp in
@@ -1037,6 +1050,9 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
 constexpr int kMixedKernel = 0;
 constexpr int kChainKernel = -1;
 constexpr int kStreamKernel = -2;  // simple cubic lattices streamed from HBM (any even L)
+// simple cubic lattices of one size L streamed from HBM, compiled for that L
+__host__ __device__ constexpr int stream_variant(int L) { return -1000 - L; }
+__host__ __device__ constexpr int stream_variant_L(int v) { return v <= -1000 ? -1000 - v : 0; }
 
 template <typename Real, int kLattice>
 __device__ __forceinline__ void dispatch_path(const DevSystem& sy, int sys_idx, int64_t path,
@@ -1051,7 +1067,7 @@ template <typename Real, int kLattice>
 struct CtaLimit {
   static constexpr int value =
       (sizeof(Real) == 8 || (kLattice > 0 && kLattice <= 16) || kLattice == kChainKernel ||
-       kLattice == kStreamKernel || kLattice == kMixedKernel)
+       kLattice == kStreamKernel || kLattice == kMixedKernel || stream_variant_L(kLattice) > 0)
           ? 512
                                                                                            : kMaxCta;
 };
@@ -1073,12 +1089,24 @@ __global__ void __launch_bounds__(CtaLimit<Real, kLattice>::value, 1)
     const int tid = static_cast<int>(threadIdx.x) - g * sy.tp;
     if (g < it.count) {
       bool done = false;
-      if constexpr (kLattice == kStreamKernel || kLattice == kMixedKernel) {
+      if constexpr (stream_variant_L(kLattice) > 0) {
+        Real* lat = reinterpret_cast<Real*>(
+            static_cast<unsigned char*>(P.lattice) +
+            (static_cast<int64_t>(blockIdx.x) * P.lattice_groups + g) * P.lattice_stride);
+        constexpr int kL = stream_variant_L(kLattice);
+        if (sy.tp == 8 * kL)  // 16 row groups of L/2 threads: L/16 rows per thread
+          run_path_streamed<Real, kL, 16>(sy, it.sys, it.path0 + g, P, smem + g * sy.slice_bytes,
+                                          tid, sy.tp, 1 + g, lat);
+        else
+          run_path_streamed<Real, kL, 0>(sy, it.sys, it.path0 + g, P, smem + g * sy.slice_bytes,
+                                         tid, sy.tp, 1 + g, lat);
+        done = true;
+      } else if constexpr (kLattice == kStreamKernel || kLattice == kMixedKernel) {
         if (sy.mode == kModeStreamed) {
           Real* lat = reinterpret_cast<Real*>(
               static_cast<unsigned char*>(P.lattice) +
               (static_cast<int64_t>(blockIdx.x) * P.lattice_groups + g) * P.lattice_stride);
-          run_path_streamed<Real>(sy, it.sys, it.path0 + g, P, smem + g * sy.slice_bytes, tid,
+          run_path_streamed<Real, 0, 0>(sy, it.sys, it.path0 + g, P, smem + g * sy.slice_bytes, tid,
                                   sy.tp, 1 + g, lat);
           done = true;
         }

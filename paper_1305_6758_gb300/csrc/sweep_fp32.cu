@@ -14,7 +14,7 @@ __device__ __forceinline__ void dispatch_path(const DevSystem& sy, int sys_idx, 
                                               int tp, int bar) {
   if constexpr (kLattice > 0) {
     run_path<Real>(GeomSC<kLattice>{}, sy, sys_idx, path, P, slice, tid, tp, bar);
-  } else if constexpr (kLattice == kStreamKernel) {
+  } else if constexpr (kLattice == kStreamKernel || stream_variant_L(kLattice) > 0) {
     // streamed paths are run by the kernel itself; nothing in shared memory only
   } else if constexpr (kLattice == kChainKernel) {
     run_path<Real>(GeomChain{sy.N}, sy, sys_idx, path, P, slice, tid, tp, bar);
@@ -42,6 +42,8 @@ static const void* kernel_of(int variant) {
     case kMixedKernel: return reinterpret_cast<const void*>(sweep_kernel<REAL, kMixedKernel>);
     case kChainKernel: return reinterpret_cast<const void*>(sweep_kernel<REAL, kChainKernel>);
     case kStreamKernel: return reinterpret_cast<const void*>(sweep_kernel<REAL, kStreamKernel>);
+    case stream_variant(64):
+      return reinterpret_cast<const void*>(sweep_kernel<REAL, stream_variant(64)>);
 #define MPK_CASE(LL) \
     case LL: return reinterpret_cast<const void*>(sweep_kernel<REAL, LL>);
       MPK_FOR_EACH_L(MPK_CASE)

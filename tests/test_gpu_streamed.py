@@ -96,6 +96,17 @@ def test_full_size_l64_launch_first_sweep():
     assert bad <= 1, f"{bad} of {total} sampled paths differ"
 
 
+@pytest.mark.parametrize("tp", [256, 384, 512])
+def test_l64_kernel_every_row_layout(tp):
+    """The kernel compiled for L = 64: 16 row groups (compile-time rows), 8 and
+    12 row groups (rows at run time): two sweeps of a few paths against the oracle."""
+    systems = [mp.System(64, 1.44, n_paths=3)]
+    recs, _ = gpu_records(systems, 1, 1, seed=6, threads_per_path=tp)
+    refs = O.run([osys(systems[0])], 1, 1, seed=6)
+    bad = sum(int(np.max(np.abs(g[FIELDS] - r[FIELDS])) > 1e-5) for g, r in zip(recs[0], refs[0]))
+    assert bad <= 1, f"{bad} of 3 paths differ"
+
+
 def test_stalled_bulk_copy_reports_timeout():
     """Failure detection: a bulk copy that is never issued makes the bounded
     mbarrier wait give up (about 2 s); the host reads MP_ETIMEOUT, the context
