@@ -112,6 +112,38 @@ OPS_PER_ATTEMPT_ISING = 25
 BYTES_PER_ATTEMPT_FP32 = 24
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the dominant kernel, from ncu captures of the kernels built from the sources
+# with this hash (sha256 over csrc/, first 16 hex digits); any change of the
+# sources voids it and the roofline reports traffic null.  sc16: the timed
+# launch of the default command, captured at full size (one ncu pass).  large:
+# a 10 + 10-sweep capture, 18.7 GB one-off (initial state, read-out) plus
+# 19.33 GB per sweep, scaled to 500 + 1000 sweeps.
+TRAFFIC = {
+    "sc16": {"sources": "6fde0b5fc455e5ae", "bytes": 1.25e6},
+    "large": {"sources": "6fde0b5fc455e5ae", "bytes": 18.7e9 + 1500 * 19.325e9},
+}
+
+
+def sources_hash() -> str:
+    import hashlib
+
+    d = os.path.join(ROOT, "paper_1305_6758_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        h.update(f.encode())
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def launch_traffic(name: str):
+    t = TRAFFIC.get(name)
+    if t and t["sources"] == sources_hash():
+        return t["bytes"]
+    return None
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -245,6 +277,7 @@ def main():
     ap.add_argument("--n-meas", type=int, default=None)
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
+    full_size = args.n_therm is None and args.n_meas is None
     if args.n_therm is not None:
         w["n_therm"] = args.n_therm
     if args.n_meas is not None:
@@ -351,7 +384,8 @@ def main():
         peak = float(peaks["hbm_gbs"])
         achieved = BYTES_PER_ATTEMPT_FP32 * kernel_rate / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "bytes_per_attempt": BYTES_PER_ATTEMPT_FP32,
+                "traffic": launch_traffic(args.workload) if full_size else None,
+                "bytes_per_attempt": BYTES_PER_ATTEMPT_FP32,
                 "peak_basis": f"{peak_kind} HBM copy bandwidth"}
     else:
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -359,7 +393,7 @@ def main():
         ops = OPS_PER_ATTEMPT_ISING if w["bound"] == "alu_ising" else OPS_PER_ATTEMPT
         achieved = ops * kernel_rate / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": None, "ops_per_attempt": ops,
+                "traffic": launch_traffic(args.workload) if full_size else None, "ops_per_attempt": ops,
                 "peak_basis": f"{n_sm} SMs x 128 lanes x {sm_max:.0f} MHz ({peak_kind} max clock)"}
     kernel = {"ising": "ising_kernel", "random_site": "random_site_kernel"}.get(
         "ising" if w["bound"] == "alu_ising" else w.get("flags"), "sweep_kernel")

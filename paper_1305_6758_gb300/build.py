@@ -21,9 +21,12 @@ LIB = os.path.join(HERE, "libmp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 # per-file extra flags: the FP32 sweep flushes denormals (its uniforms are >= 2^-24)
-EXTRA = {"sweep_fp32.cu": ["-ftz=true"]}
-SOURCES = ["mp_api.cu", "reduce.cu", "sweep_fp32.cu", "sweep_fp64.cu", "ising.cu", "random_site.cu",
-           "noalloc.cu"]
+EXTRA = {f: ["-ftz=true"] for f in ("sweep_fp32.cu", "sweep_fp32_b.cu", "sweep_fp32_c.cu", "sweep_fp32_d.cu")}
+# the sweep kernels are spread over four translation units per precision so
+# that they compile in parallel
+SOURCES = ["mp_api.cu", "reduce.cu", "sweep_fp32.cu", "sweep_fp32_b.cu", "sweep_fp32_c.cu",
+           "sweep_fp32_d.cu", "sweep_fp64.cu", "sweep_fp64_b.cu", "sweep_fp64_c.cu", "sweep_fp64_d.cu",
+           "ising.cu", "random_site.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

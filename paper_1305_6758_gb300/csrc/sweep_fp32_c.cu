@@ -1,0 +1,22 @@
+// FP32 sweep kernels, part c: the largest shared-memory sizes, chains and the streamed kernels.
+// (The host entry points and part a are in sweep_fp32.cu.)
+#define REAL float
+#define SUFFIX(f) f##_fp32
+#define MPK_FOR_EACH_L MPK_FOR_EACH_L_FP32
+#include "sweep_inst.cuh"
+
+namespace mpk {
+
+const void* SUFFIX(sweep_part_c)(int variant) {
+  switch (variant) {
+    MPK_PART_CASE(22)
+    MPK_PART_CASE(24)
+    MPK_PART_CASE(26)
+    MPK_PART_CASE(kChainKernel)
+    MPK_PART_CASE(kStreamKernel)
+    MPK_PART_CASE(stream_variant(64))
+    default: return nullptr;
+  }
+}
+
+}  // namespace mpk

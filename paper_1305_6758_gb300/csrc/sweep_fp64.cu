@@ -1,55 +1,35 @@
 // FP64 form of the shared-memory sweep (the plain FP64 GPU form): FP64 spins,
 // energy differences, Boltzmann factors and accumulators.
-#include "kernels.h"
+// This file holds part a (the smallest shared-memory lattice sizes) and the
+// host entry points; parts b, c and d are sweep_fp64_b.cu, _c.cu and _d.cu.
 #define REAL double
 #define SUFFIX(f) f##_fp64
 #define MPK_FOR_EACH_L MPK_FOR_EACH_L_FP64
-#include "sweep.cuh"
+#include "sweep_inst.cuh"
 
 namespace mpk {
 
-template <typename Real, int kLattice>
-__device__ __forceinline__ void dispatch_path(const DevSystem& sy, int sys_idx, int64_t path,
-                                              const SweepParams& P, unsigned char* slice, int tid,
-                                              int tp, int bar) {
-  if constexpr (kLattice > 0) {
-    run_path<Real>(GeomSC<kLattice>{}, sy, sys_idx, path, P, slice, tid, tp, bar);
-  } else if constexpr (kLattice == kStreamKernel || stream_variant_L(kLattice) > 0) {
-    // streamed paths are run by the kernel itself; nothing in shared memory only
-  } else if constexpr (kLattice == kChainKernel) {
-    run_path<Real>(GeomChain{sy.N}, sy, sys_idx, path, P, slice, tid, tp, bar);
-  } else {
-    if (sy.lattice == MP_LATTICE_CHAIN) {
-      run_path<Real>(GeomChain{sy.N}, sy, sys_idx, path, P, slice, tid, tp, bar);
-      return;
-    }
-    switch (sy.L) {
-#define MPK_CASE(LL)                                                           \
-  case LL:                                                                     \
-    run_path<Real>(GeomSC<LL>{}, sy, sys_idx, path, P, slice, tid, tp, bar);   \
-    break;
-      MPK_FOR_EACH_L(MPK_CASE)
-#undef MPK_CASE
-      default:
-        break;
-    }
-  }
-}
-
-// kernel of a variant (simple cubic L, chain, or mixed); nullptr if not built
-static const void* kernel_of(int variant) {
+const void* SUFFIX(sweep_part_a)(int variant) {
   switch (variant) {
-    case kMixedKernel: return reinterpret_cast<const void*>(sweep_kernel<REAL, kMixedKernel>);
-    case kChainKernel: return reinterpret_cast<const void*>(sweep_kernel<REAL, kChainKernel>);
-    case kStreamKernel: return reinterpret_cast<const void*>(sweep_kernel<REAL, kStreamKernel>);
-    case stream_variant(64):
-      return reinterpret_cast<const void*>(sweep_kernel<REAL, stream_variant(64)>);
-#define MPK_CASE(LL) \
-    case LL: return reinterpret_cast<const void*>(sweep_kernel<REAL, LL>);
-      MPK_FOR_EACH_L(MPK_CASE)
-#undef MPK_CASE
+    MPK_PART_CASE(2)
+    MPK_PART_CASE(4)
+    MPK_PART_CASE(6)
+    MPK_PART_CASE(8)
+    MPK_PART_CASE(10)
     default: return nullptr;
   }
+}
+const void* SUFFIX(sweep_part_b)(int variant);
+const void* SUFFIX(sweep_part_c)(int variant);
+const void* SUFFIX(sweep_part_d)(int variant);
+
+// kernel of a variant (simple cubic L, chain, streamed or mixed); nullptr if not built
+static const void* kernel_of(int variant) {
+  const void* k = SUFFIX(sweep_part_a)(variant);
+  if (!k) k = SUFFIX(sweep_part_b)(variant);
+  if (!k) k = SUFFIX(sweep_part_c)(variant);
+  if (!k) k = SUFFIX(sweep_part_d)(variant);
+  return k;
 }
 
 bool SUFFIX(sweep_supports_L)(int L) { return L > 0 && kernel_of(L) != nullptr; }
