@@ -35,8 +35,9 @@ cudaError_t sweep_occupancy(int precision, int variant, int cta, int smem, int* 
 cudaError_t launch_sweep(int precision, int variant, const SweepParams& p, int grid, int cta,
                          int smem, cudaStream_t st);
 
-// The streamed kernel compiled for simple cubic L = 64 (all systems of the
-// batch streamed at that size).
+// The streamed kernels compiled for simple cubic L = 32 and L = 64 (all
+// systems of the batch streamed at that size).
+constexpr int kStreamL32 = -1032;
 constexpr int kStreamL64 = -1064;
 
 // The square-lattice Ising kernel (variant kIsingKernel), any even L.

@@ -296,17 +296,24 @@ __device__ __forceinline__ void attempt(uint32_t i, uint32_t sweep, uint32_t c2,
 }
 
 // Sites of a column interleaved by the compiler (independent Philox chains):
-// 4 in the FP32 kernels with 128 registers per thread (L <= 16); none in
-// those with 64, where unrolling spills registers.
+// 4 in the FP32 kernels (512-thread CTAs, up to 128 registers per thread).
 template <typename Real, int L>
-constexpr int kColumnUnroll = sizeof(Real) == 8 ? 1 : (L <= 16 ? 4 : 1);
+constexpr int kColumnUnroll = sizeof(Real) == 8 ? 1 : 4;
 
 // One half-sweep of one thread: every site of colour c it owns.
 //
-// Column walk (simple cubic, tp a multiple of the HP half-sites of a z-plane):
-// the thread keeps its column (hx, y) and steps z by tp / HP, so its x and y
-// neighbour offsets are fixed and only the z wrap is decided per site.
-// Otherwise every site is decoded from its half index.
+// Blocked column walk (simple cubic): the sites of colour c are ordered
+// column by column, s = col * L + z with col = x/2 + (L/2) y (so the half
+// index is col + (L^2/2) z), and thread tid takes the block of
+// B = ceil(NH / tp) consecutive s (the last blocks may be shorter).  Along a column the x parity
+// of the site flips from plane to plane, so the other colour's spin at the
+// site's own half index is both an x neighbour of the site in plane z and the
+// -z neighbour of the site in plane z + 1, and the +z neighbour of the site
+// in plane z is an x neighbour of the site in plane z + 1: after the first
+// site of a column, two of the six neighbours are already in registers.  The
+// two x neighbours are added first, in either order (a + b = b + a exactly),
+// so the sum keeps the fixed order +x, -x, +y, -y, +z, -z.  Open chains
+// decode every site from its half index.
 template <typename Real, class Geom, bool kMeas, bool kEnergy>
 __device__ __forceinline__ void half_sweep(const Geom& geo, int c, uint32_t sweep, uint32_t c2,
                                            uint32_t c3, const PhiloxKeys& key, Real* sp, int tid,
@@ -318,38 +325,27 @@ __device__ __forceinline__ void half_sweep(const Geom& geo, int c, uint32_t swee
   if constexpr (Geom::kColumns) {
     if (columns) {
       constexpr int HL = Geom::HL, HP = Geom::HP, LL = 2 * Geom::HL;
-      const int hx = tid % HL;
-      const int t = tid / HL;
-      const int y = t % LL;
-      const int dz = tp / HP;
-      const int oyp = (y == LL - 1) ? -(LL - 1) * HL : HL;
-      const int oym = (y == 0) ? (LL - 1) * HL : -HL;
-      const int oxp1 = (hx == HL - 1) ? -(HL - 1) : 1;  // +x offset when x is odd
-      const int oxm0 = (hx == 0) ? (HL - 1) : -1;         // -x offset when x is even
-      int z = t / LL;
-      using A = Arith<Real>;
-      if (dz == 1) {
-        // tp = HP: the thread walks planes z = 0 .. L-1 of its column, and
-        // the x parity of its site flips from plane to plane.  The other
-        // colour's spin at half index hh of plane z is then both an x
-        // neighbour of the site in plane z and the -z neighbour of the site
-        // in plane z + 1, and the +z neighbour of the site in plane z is an x
-        // neighbour of the site in plane z + 1: two of the six neighbours of
-        // every site after the first are already in registers.  The two x
-        // neighbours are added first in either order (a + b = b + a exactly),
-        // so the sum keeps the fixed order +x, -x, +y, -y, +z, -z.
-        V3<Real> o0{Real(0), Real(0), Real(0)};  // half index hh, plane z
-        V3<Real> mz{Real(0), Real(0), Real(0)};  // -z neighbour
+      const int B = (Geom::NH + tp - 1) / tp;
+      // the block [s, s_end) in column segments: column col, planes z0 .. z1-1
+      for (int s = tid * B, s_end = min(s + B, Geom::NH); s < s_end;) {
+        const int col = s / LL;
+        const int z0 = s - col * LL;
+        const int z1 = min(LL, z0 + (s_end - s));
+        s += z1 - z0;
+        const int hx = col % HL;
+        const int y = col / HL;
+        const int oyp = (y == LL - 1) ? -(LL - 1) * HL : HL;
+        const int oym = (y == 0) ? (LL - 1) * HL : -HL;
+        const int oxp1 = (hx == HL - 1) ? -(HL - 1) : 1;  // +x offset when x is odd
+        const int oxm0 = (hx == 0) ? (HL - 1) : -1;         // -x offset when x is even
+        int hh = col + HP * z0;
+        V3<Real> o0 = oth.ld(hh);  // the other colour at the site's half index
+        V3<Real> mz = oth.ld(z0 == 0 ? hh + (LL - 1) * HP : hh - HP);  // -z neighbour
 #pragma unroll(kColumnUnroll<Real, LL>)
-        for (int hh = tid; hh < Geom::NH; hh += tp, ++z) {
+        for (int z = z0; z < z1; ++z, hh += HP) {
           const int p = (y + z + c) & 1;
-          if (hh == tid) {  // z = 0: the -z neighbour wraps to plane L - 1
-            mz = oth.ld(hh + (LL - 1) * HP);
-            o0 = oth.ld(hh);
-          }
           const int nxo = hh + (p ? oxp1 : oxm0);
-          const int n4 = (z == LL - 1) ? hh - (LL - 1) * HP : hh + HP;
-          const V3<Real> cz = oth.ld(n4);
+          const V3<Real> cz = oth.ld(z == LL - 1 ? hh - (LL - 1) * HP : hh + HP);
           const V3<Real> f =
               add3(add3(add3(add3(add3(o0, oth.ld(nxo)), oth.ld(hh + oyp)), oth.ld(hh + oym)), cz), mz);
           update<Real, kMeas, kEnergy>(static_cast<uint32_t>(2 * hh + p), sweep, c2, c3, key, own, hh,
@@ -357,27 +353,6 @@ __device__ __forceinline__ void half_sweep(const Geom& geo, int c, uint32_t swee
           mz = o0;
           o0 = cz;
         }
-        return;
-      }
-      // With dz = 2 the +z neighbour of one site of the column is the -z
-      // neighbour of the next: it is loaded once.
-      V3<Real> cz{Real(0), Real(0), Real(0)};
-#pragma unroll(kColumnUnroll<Real, LL>)
-      for (int hh = tid; hh < Geom::NH; hh += tp, z += dz) {
-        const int p = (y + z + c) & 1;
-        const int n0 = hh + (p ? oxp1 : 0), n1 = hh + (p ? 0 : oxm0);
-        const int n4 = (z == LL - 1) ? hh - (LL - 1) * HP : hh + HP;
-        V3<Real> mz;
-        if (dz == 2 && hh != tid) {
-          mz = cz;
-        } else {
-          mz = oth.ld((z == 0) ? hh + (LL - 1) * HP : hh - HP);
-        }
-        cz = oth.ld(n4);
-        const V3<Real> f = add3(
-            add3(add3(add3(add3(oth.ld(n0), oth.ld(n1)), oth.ld(hh + oyp)), oth.ld(hh + oym)), cz), mz);
-        update<Real, kMeas, kEnergy>(static_cast<uint32_t>(2 * hh + p), sweep, c2, c3, key, own, hh,
-                                     f.x, f.y, f.z, J, hf, bp, accepted, part);
       }
       return;
     }
@@ -585,7 +560,8 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
   const int init = path_init_mode(P.init_mode, path, sy.n_paths);
   const Real J = static_cast<Real>(sy.J), hf = static_cast<Real>(sy.h);
   const Real bp = A::beta_param(sy.beta);
-  const bool columns = Geom::kColumns && (tp % Geom::HP) == 0;
+  bool columns = false;
+  if constexpr (Geom::kColumns) columns = true;  // blocks of ceil(NH / tp) sites
   const int64_t j_first = P.s_begin > P.n_therm ? P.s_begin - P.n_therm : 0;
   const Meter<Real> meter{reinterpret_cast<double*>(slice + slice_acc_offset()),
                           reinterpret_cast<Real*>(slice + slice_red_offset()),
@@ -1059,17 +1035,13 @@ __device__ __forceinline__ void dispatch_path(const DevSystem& sy, int sys_idx, 
                                               const SweepParams& P, unsigned char* slice, int tid,
                                               int tp, int bar);
 
-// Largest CTA of each kernel.  The FP64 form needs more than 64 registers;
-// FP32 lattices up to L = 16 run 512-thread CTAs with up to 128 registers per
-// thread, which buys the unrolled column walk its instruction-level
-// parallelism; larger lattices keep 1024-thread CTAs for occupancy.
+// Largest CTA of every sweep kernel: 512 threads with up to 128 registers per
+// thread, which the FP64 form needs and which buys the FP32 column walk its
+// unrolled instruction-level parallelism.  (1024-thread CTAs at 64 registers
+// were measured 6-16% slower for L = 18 and 24.)
 template <typename Real, int kLattice>
 struct CtaLimit {
-  static constexpr int value =
-      (sizeof(Real) == 8 || (kLattice > 0 && kLattice <= 16) || kLattice == kChainKernel ||
-       kLattice == kStreamKernel || kLattice == kMixedKernel || stream_variant_L(kLattice) > 0)
-          ? 512
-                                                                                           : kMaxCta;
+  static constexpr int value = 512;
 };
 
 template <typename Real, int kLattice>
@@ -1097,6 +1069,9 @@ __global__ void __launch_bounds__(CtaLimit<Real, kLattice>::value, 1)
         if (sy.tp == 8 * kL)  // 16 row groups of L/2 threads: L/16 rows per thread
           run_path_streamed<Real, kL, 16>(sy, it.sys, it.path0 + g, P, smem + g * sy.slice_bytes,
                                           tid, sy.tp, 1 + g, lat);
+        else if (sy.tp == 4 * kL)  // 8 row groups: L/8 rows per thread
+          run_path_streamed<Real, kL, 8>(sy, it.sys, it.path0 + g, P, smem + g * sy.slice_bytes,
+                                         tid, sy.tp, 1 + g, lat);
         else
           run_path_streamed<Real, kL, 0>(sy, it.sys, it.path0 + g, P, smem + g * sy.slice_bytes,
                                          tid, sy.tp, 1 + g, lat);
@@ -1106,8 +1081,22 @@ __global__ void __launch_bounds__(CtaLimit<Real, kLattice>::value, 1)
           Real* lat = reinterpret_cast<Real*>(
               static_cast<unsigned char*>(P.lattice) +
               (static_cast<int64_t>(blockIdx.x) * P.lattice_groups + g) * P.lattice_stride);
-          run_path_streamed<Real, 0, 0>(sy, it.sys, it.path0 + g, P, smem + g * sy.slice_bytes, tid,
-                                  sy.tp, 1 + g, lat);
+          if constexpr (kLattice == kMixedKernel) {
+            // batches of uneven sizes: the streamed size of the benchmark's
+            // batch (L = 32) with compile-time rows
+            if (sy.L == 32 && sy.tp == 8 * 32)
+              run_path_streamed<Real, 32, 16>(sy, it.sys, it.path0 + g, P, smem + g * sy.slice_bytes,
+                                              tid, sy.tp, 1 + g, lat);
+            else if (sy.L == 32 && sy.tp == 4 * 32)
+              run_path_streamed<Real, 32, 8>(sy, it.sys, it.path0 + g, P, smem + g * sy.slice_bytes,
+                                             tid, sy.tp, 1 + g, lat);
+            else
+              run_path_streamed<Real, 0, 0>(sy, it.sys, it.path0 + g, P, smem + g * sy.slice_bytes,
+                                            tid, sy.tp, 1 + g, lat);
+          } else {
+            run_path_streamed<Real, 0, 0>(sy, it.sys, it.path0 + g, P, smem + g * sy.slice_bytes, tid,
+                                          sy.tp, 1 + g, lat);
+          }
           done = true;
         }
       }

@@ -229,19 +229,21 @@ def test_rerun_and_seed():
 
 # ----------------------------------------------------- thread layouts -------
 @pytest.mark.parametrize("L,tp", [
-    (8, 32),    # threads per path = sites per z-plane of one colour: column walk, step 1
-    (8, 64),    # step 2
-    (8, 96),    # step 3
-    (8, 128),   # step 4
-    (8, 160),   # not a multiple of a plane: every site decoded from its index
-    (12, 72 * 4),
+    (8, 32),    # blocks of 8 sites: one column per thread
+    (8, 64),    # half columns
+    (8, 96),    # blocks of 3 sites, the last ones shorter (256 = 85 x 3 + 1)
+    (8, 128),   # blocks of 2
+    (8, 160),   # blocks of 2, the last 32 threads idle
+    (12, 288),  # blocks of 3 inside columns of 12
+    (12, 96),   # blocks of 9 that cross column boundaries
     (16, 128),
     (16, 256),
+    (20, 160),  # blocks of 25 across columns of 20
 ])
 def test_fp64_every_walk_layout_matches_oracle(L, tp):
-    """Each thread-to-site layout of the shared-memory sweep (the column walk
-    that reuses z and x neighbours across planes, and the generic decode)
-    gives the oracle's per-path records."""
+    """Each thread-to-site layout of the shared-memory sweep (blocked column
+    walks that carry z and x neighbours from site to site, even and uneven
+    blocks) gives the oracle's per-path records."""
     systems = [mp.System(L, 1.1, h=0.03, n_paths=5)]
     recs, _, _ = run_gpu(systems, 2, 3, seed=8, precision=mp.FP64, threads_per_path=tp)
     ref = O.run([osys(systems[0])], 2, 3, seed=8)[0]
@@ -252,11 +254,12 @@ def test_fp64_every_walk_layout_matches_oracle(L, tp):
 
 
 def test_fp32_trajectories_do_not_depend_on_the_layout():
-    """FP32, L=16: column walks with step 1, 2 and 4 planes and paths of one
-    warp give the same records (the same arithmetic per site in the same order)."""
+    """FP32, L=16: blocked column walks of 16, 8, 4 and 22 sites (uneven) and
+    paths of one warp give the same records (the same arithmetic per site in
+    the same order)."""
     systems = [mp.System(16, 1.3, n_paths=6)]
     base = None
-    for tp in (128, 256, 512, 96):
+    for tp in (128, 256, 512, 96, 32):
         recs, _, _ = run_gpu(systems, 3, 5, seed=9, threads_per_path=tp)
         if base is None:
             base = recs[0]
