@@ -654,15 +654,13 @@ std::vector<int> tp_candidates(mp_state* h, int k, int cta_max) {
     for (int r : {2, 4, 8}) add(std::max(HL, HL * ((sy.L + r - 1) / r)));
     return c;
   }
-  if (sy.lattice == MP_LATTICE_SC) {  // blocked column walks: divisors of the sites per colour
-    for (int t = 32; t <= std::min(cta_max, NH); t += 32)
-      if (NH % t == 0 && NH / t >= 2 && NH / t <= 48) add(t);
-  }
-  for (int t : {32, 64, 96, 128, 192, 256, 384, 512, 768, 1024}) {
+  // every multiple of 32 with 2 .. 48 sites per thread (at most 16 with
+  // 512-thread CTAs): the column-segment walk runs any of them, and how well
+  // a count splits the columns is easier to measure than to model
+  for (int t = 32; t <= std::min(cta_max, NH); t += 32) {
     const double sites = static_cast<double>(NH) / t;
-    if (sites >= 2.0 && sites <= 40.0) add(t);
+    if (sites >= 2.0 && sites <= 48.0) add(t);
   }
-  if (c.size() > 8) c.resize(8);
   return c;
 }
 

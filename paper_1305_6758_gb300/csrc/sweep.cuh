@@ -302,36 +302,37 @@ constexpr int kColumnUnroll = sizeof(Real) == 8 ? 1 : 4;
 
 // One half-sweep of one thread: every site of colour c it owns.
 //
-// Blocked column walk (simple cubic): the sites of colour c are ordered
-// column by column, s = col * L + z with col = x/2 + (L/2) y (so the half
-// index is col + (L^2/2) z), and thread tid takes the block of
-// B = ceil(NH / tp) consecutive s (the last blocks may be shorter).  Along a column the x parity
-// of the site flips from plane to plane, so the other colour's spin at the
-// site's own half index is both an x neighbour of the site in plane z and the
-// -z neighbour of the site in plane z + 1, and the +z neighbour of the site
-// in plane z is an x neighbour of the site in plane z + 1: after the first
-// site of a column, two of the six neighbours are already in registers.  The
-// two x neighbours are added first, in either order (a + b = b + a exactly),
-// so the sum keeps the fixed order +x, -x, +y, -y, +z, -z.  Open chains
-// decode every site from its half index.
+// Column-segment walk (simple cubic, K > 0): a colour's sites form L^2/2
+// columns col = x/2 + (L/2) y of L planes each (half index col + (L^2/2) z);
+// each column is cut into K segments of L/K planes, and the HP * K units
+// (column col, segment g), numbered u = g * HP + col, are dealt out to the
+// threads round by round (thread tid takes u = tid, tid + tp, ...), so the
+// lanes of a warp work on consecutive columns of the same planes and their
+// shared-memory accesses are consecutive elements.  Within a segment the +-x
+// and +-y neighbour offsets are fixed, and since the x parity flips from
+// plane to plane, the other colour's spin at the site's own half index is
+// both an x neighbour of the site in plane z and the -z neighbour of the site
+// in plane z + 1, while the +z neighbour of one site is an x neighbour of the
+// next: after the first site of a segment two of the six neighbours are
+// already in registers.  The two x neighbours are added first, in either
+// order (a + b = b + a exactly), so the sum keeps the fixed order +x, -x, +y,
+// -y, +z, -z.  K = 0: every site decoded from its half index (open chains).
 template <typename Real, class Geom, bool kMeas, bool kEnergy>
 __device__ __forceinline__ void half_sweep(const Geom& geo, int c, uint32_t sweep, uint32_t c2,
                                            uint32_t c3, const PhiloxKeys& key, Real* sp, int tid,
-                                           int tp, bool columns, Real J, Real hf, Real bp,
+                                           int tp, int K, Real J, Real hf, Real bp,
                                            int& accepted, Partials<Real>& part) {
   const int S = geo.stride();
   const SpinView<Real> own(sp + c * 3 * S, S);
   const SpinView<Real> oth(sp + (1 - c) * 3 * S, S);
   if constexpr (Geom::kColumns) {
-    if (columns) {
+    if (K > 0) {
       constexpr int HL = Geom::HL, HP = Geom::HP, LL = 2 * Geom::HL;
-      const int B = (Geom::NH + tp - 1) / tp;
-      // the block [s, s_end) in column segments: column col, planes z0 .. z1-1
-      for (int s = tid * B, s_end = min(s + B, Geom::NH); s < s_end;) {
-        const int col = s / LL;
-        const int z0 = s - col * LL;
-        const int z1 = min(LL, z0 + (s_end - s));
-        s += z1 - z0;
+      const int seg = LL / K;  // planes per segment
+      for (int u = tid; u < HP * K; u += tp) {
+        const int g = u / HP;
+        const int col = u - g * HP;
+        const int z0 = g * seg;
         const int hx = col % HL;
         const int y = col / HL;
         const int oyp = (y == LL - 1) ? -(LL - 1) * HL : HL;
@@ -342,7 +343,7 @@ __device__ __forceinline__ void half_sweep(const Geom& geo, int c, uint32_t swee
         V3<Real> o0 = oth.ld(hh);  // the other colour at the site's half index
         V3<Real> mz = oth.ld(z0 == 0 ? hh + (LL - 1) * HP : hh - HP);  // -z neighbour
 #pragma unroll(kColumnUnroll<Real, LL>)
-        for (int z = z0; z < z1; ++z, hh += HP) {
+        for (int z = z0; z < z0 + seg; ++z, hh += HP) {
           const int p = (y + z + c) & 1;
           const int nxo = hh + (p ? oxp1 : oxm0);
           const V3<Real> cz = oth.ld(z == LL - 1 ? hh - (LL - 1) * HP : hh + HP);
@@ -560,8 +561,23 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
   const int init = path_init_mode(P.init_mode, path, sy.n_paths);
   const Real J = static_cast<Real>(sy.J), hf = static_cast<Real>(sy.h);
   const Real bp = A::beta_param(sy.beta);
-  bool columns = false;
-  if constexpr (Geom::kColumns) columns = true;  // blocks of ceil(NH / tp) sites
+  // column segments per column: the divisor K of L that spreads the HP * K
+  // units most evenly over the tp threads (the smallest such K, for the
+  // longest segments); 0 = decode every site (open chains)
+  int K = 0;
+  if constexpr (Geom::kColumns) {
+    constexpr int LL = 2 * Geom::HL;
+    double best = -1.0;
+    for (int k = 1; k <= LL; ++k) {
+      if (LL % k) continue;
+      const int units = Geom::HP * k;
+      const double eff = static_cast<double>(units) / (static_cast<double>((units + tp - 1) / tp) * tp);
+      if (eff > best + 1e-9) {
+        best = eff;
+        K = k;
+      }
+    }
+  }
   const int64_t j_first = P.s_begin > P.n_therm ? P.s_begin - P.n_therm : 0;
   const Meter<Real> meter{reinterpret_cast<double*>(slice + slice_acc_offset()),
                           reinterpret_cast<Real*>(slice + slice_red_offset()),
@@ -602,14 +618,14 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
     Partials<Real> part{Real(0), Real(0), Real(0), Real(0)};
     poll_cancel(P, s, tid, &cancel_flag[gidx]);
     if (s < P.n_therm) {
-      half_sweep<Real, Geom, false, false>(geo, 0, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf,
+      half_sweep<Real, Geom, false, false>(geo, 0, sw, c2, c3u, P.key, sp, tid, tp, K, J, hf,
                                            bp, accepted, part);
       group_sync(tp, bar);
       if (cancel_flag[gidx]) {
         canceled = true;
         break;
       }
-      half_sweep<Real, Geom, false, false>(geo, 1, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf,
+      half_sweep<Real, Geom, false, false>(geo, 1, sw, c2, c3u, P.key, sp, tid, tp, K, J, hf,
                                            bp, accepted, part);
       group_sync(tp, bar);
       continue;
@@ -617,7 +633,7 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
     // Measurement sweep j.  Colour-0 sites keep their values during the
     // colour-1 pass, so the colour-1 local fields give every bond once.
     const int64_t j = s - P.n_therm;
-    half_sweep<Real, Geom, true, false>(geo, 0, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf, bp,
+    half_sweep<Real, Geom, true, false>(geo, 0, sw, c2, c3u, P.key, sp, tid, tp, K, J, hf, bp,
                                         accepted, part);
     group_sync(tp, bar);
     if (cancel_flag[gidx]) {
@@ -625,7 +641,7 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
       break;
     }
     meter.maybe_flush(j);
-    half_sweep<Real, Geom, true, true>(geo, 1, sw, c2, c3u, P.key, sp, tid, tp, columns, J, hf, bp,
+    half_sweep<Real, Geom, true, true>(geo, 1, sw, c2, c3u, P.key, sp, tid, tp, K, J, hf, bp,
                                        accepted, part);
     meter.record(j, part);
     group_sync(tp, bar);

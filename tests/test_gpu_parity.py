@@ -229,21 +229,21 @@ def test_rerun_and_seed():
 
 # ----------------------------------------------------- thread layouts -------
 @pytest.mark.parametrize("L,tp", [
-    (8, 32),    # blocks of 8 sites: one column per thread
-    (8, 64),    # half columns
-    (8, 96),    # blocks of 3 sites, the last ones shorter (256 = 85 x 3 + 1)
-    (8, 128),   # blocks of 2
-    (8, 160),   # blocks of 2, the last 32 threads idle
-    (12, 288),  # blocks of 3 inside columns of 12
-    (12, 96),   # blocks of 9 that cross column boundaries
-    (16, 128),
+    (8, 32),    # one whole column of 8 planes per thread
+    (8, 64),    # columns cut in 2 segments
+    (8, 96),    # 8 segments of 1 plane, dealt out in rounds (some threads idle in the last)
+    (8, 128),   # 4 segments of 2 planes
+    (8, 160),   # uneven rounds
+    (12, 288),  # 4 segments of 3 planes
+    (12, 96),   # 4 segments of 3 planes over 3 rounds
+    (16, 128),  # the benchmark layout: one column per thread
     (16, 256),
-    (20, 160),  # blocks of 25 across columns of 20
+    (20, 160),  # 4 segments of 5 planes over 5 rounds
 ])
 def test_fp64_every_walk_layout_matches_oracle(L, tp):
-    """Each thread-to-site layout of the shared-memory sweep (blocked column
-    walks that carry z and x neighbours from site to site, even and uneven
-    blocks) gives the oracle's per-path records."""
+    """Each thread-to-site layout of the shared-memory sweep (column
+    segments that carry z and x neighbours from site to site, dealt out to
+    the threads in even or uneven rounds) gives the oracle's per-path records."""
     systems = [mp.System(L, 1.1, h=0.03, n_paths=5)]
     recs, _, _ = run_gpu(systems, 2, 3, seed=8, precision=mp.FP64, threads_per_path=tp)
     ref = O.run([osys(systems[0])], 2, 3, seed=8)[0]
@@ -254,7 +254,7 @@ def test_fp64_every_walk_layout_matches_oracle(L, tp):
 
 
 def test_fp32_trajectories_do_not_depend_on_the_layout():
-    """FP32, L=16: blocked column walks of 16, 8, 4 and 22 sites (uneven) and
+    """FP32, L=16: column segments of 16, 8 and 4 planes, uneven rounds and
     paths of one warp give the same records (the same arithmetic per site in
     the same order)."""
     systems = [mp.System(16, 1.3, n_paths=6)]
