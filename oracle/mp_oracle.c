@@ -335,9 +335,9 @@ static void run_path(const path_job* jb) {
  *   - a sweep flips-tests every colour-0 site, then every colour-1 site;
  *     dE = 2 s_i (J sum_nb s_j + h), accept when dE <= 0, else iff
  *     u < exp(-beta dE) with u = (r + 1/2) 2^-32;
- *   - the word r of the colour-c site with half index hh = i >> 1 is word
- *     hh mod 4 of Philox(hh / 4, sweep, path, (4 + c) | sys<<8): one call
- *     serves four sites of one colour;
+ *   - the word r of the colour-c site in row y with x/2 = hx is word y mod 4
+ *     of Philox(hx + (L/2) (y / 4), sweep, path, (4 + c) | sys<<8): one call
+ *     serves the four sites of one colour in rows 4j .. 4j+3 at the same x/2;
  *   - per sweep: e = H / N and m = sum s_i / N; the record keeps the
  *     Heisenberg layout with m_x = m_y = 0 and m_z = m. */
 static void run_path_ising(const path_job* jb) {
@@ -362,14 +362,14 @@ static void run_path_ising(const path_job* jb) {
       for (int64_t i = 0; i < N; ++i) {
         const int64_t x = i % L, y = i / L;
         if (((x + y) & 1) != c) continue;
-        const int64_t hh = i >> 1;
-        oracle_philox((uint32_t)(hh >> 2), (uint32_t)sw, c2, (OR_TAG_ISING + (uint32_t)c) | sys_hi,
-                      jb->k0, jb->k1, r);
+        const int64_t hx = x >> 1;
+        oracle_philox((uint32_t)(hx + (L / 2) * (y >> 2)), (uint32_t)sw, c2,
+                      (OR_TAG_ISING + (uint32_t)c) | sys_hi, jb->k0, jb->k1, r);
         const int64_t nb[4] = {(x + 1) % L + L * y, (x + L - 1) % L + L * y,
                                x + L * ((y + 1) % L), x + L * ((y + L - 1) % L)};
         const int hloc = s[nb[0]] + s[nb[1]] + s[nb[2]] + s[nb[3]];
         const double dE = 2.0 * (double)s[i] * (J * (double)hloc + hf);
-        if (dE <= 0.0 || u01(r[hh & 3]) < exp(-beta * dE)) {
+        if (dE <= 0.0 || u01(r[y & 3]) < exp(-beta * dE)) {
           s[i] = -s[i];
           ++accepted;
         }

@@ -11,8 +11,9 @@
 //
 // GB300 mapping: a path's spins are bytes in shared memory,
 // [colour][half index], half index i >> 1 = x/2 + (L/2) y.  One Philox call
-// serves four consecutive half indices of one colour: the word of half index
-// hh is word hh mod 4 of Philox(hh / 4, sweep, path, (4 + colour) | sys << 8).
+// serves the four sites of one colour in rows 4j .. 4j+3 at one x/2 = hx:
+// row y takes word y mod 4 of Philox(hx + (L/2) j, sweep, path,
+// (4 + colour) | sys << 8).
 // Every dE > 0 that can occur (5 neighbour sums x 2 spin signs) has its
 // acceptance turned, on the host and in FP64, into an integer threshold t
 // with u < exp(-beta dE)  <=>  r < t,  so the device test is one integer
@@ -31,7 +32,15 @@ namespace {
 constexpr int kIsingThreads = 1024;
 constexpr int kThrBytes = kIsingThrBytes;  // 10 thresholds (uint64) before the path's spins
 
-// Flip tests of colour c for this thread's groups of four half indices.
+// Flip tests of colour c for this thread's strips.  A strip is the four
+// sites of colour c in rows 4j .. 4j+3 at one x/2 = hx (strip index
+// hx + (L/2) j, which is also the Philox counter: word y mod 4 serves row y).
+// Strips are dealt out round by round, so the lanes of a warp hold
+// consecutive hx of the same rows and read consecutive bytes.  Along a strip
+// the other colour's spin at the site's own half index is an x neighbour of
+// the site in row y and the -y neighbour of the site in row y + 1, and the +y
+// neighbour of row y is that x neighbour of row y + 1: from the second row
+// on, two of the four neighbours are already in registers.
 template <bool kMeas, bool kEnergy>
 __device__ __forceinline__ void ising_half_sweep(int L, int c, uint32_t sweep, uint32_t c2,
                                                  uint32_t c3, const PhiloxKeys& key,
@@ -40,27 +49,29 @@ __device__ __forceinline__ void ising_half_sweep(int L, int c, uint32_t sweep, u
                                                  const unsigned long long* __restrict__ thr,
                                                  int tid, int tp, int& accepted, int& eb, int& ms) {
   const int HL = L >> 1;
-  const int NH = HL * L;
-  const int groups = (NH + 3) >> 2;
-  for (int g = tid; g < groups; g += tp) {
-    const Philox4 r = philox4x32_10(static_cast<uint32_t>(g), sweep, c2, c3, key);
+  const int strips = HL * ((L + 3) >> 2);
+  for (int t = tid; t < strips; t += tp) {
+    const Philox4 r = philox4x32_10(static_cast<uint32_t>(t), sweep, c2, c3, key);
     const uint32_t w[4] = {r.x, r.y, r.z, r.w};
-    int hh = g << 2;
-    int y = hh / HL;
-    int hx = hh - y * HL;
+    const int j = t / HL;
+    const int hx = t - j * HL;
+    const int oxp1 = (hx == HL - 1) ? -(HL - 1) : 1;  // +x offset when x is odd
+    const int oxm0 = (hx == 0) ? (HL - 1) : -1;         // -x offset when x is even
+    const int y0 = 4 * j;
+    int hh = hx + HL * y0;
+    int o0 = oth[hh];                                         // the site's own half index
+    int dn = oth[y0 == 0 ? hh + (L - 1) * HL : hh - HL];      // -y neighbour
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      if (hh < NH) {
+      const int y = y0 + k;
+      if (y < L) {
         const int p = (y + c) & 1;  // x = 2 hx + p
-        const int row = y * HL;
-        const int xo = p ? (hx == HL - 1 ? 0 : hx + 1) : (hx == 0 ? HL - 1 : hx - 1);
-        const int yp = (y == L - 1 ? 0 : y + 1) * HL;
-        const int ym = (y == 0 ? L - 1 : y - 1) * HL;
-        // +x and -x are {hx, xo} in either order (integer sum)
-        const int hl = oth[row + hx] + oth[row + xo] + oth[yp + hx] + oth[ym + hx];
+        const int up = oth[y == L - 1 ? hh - (L - 1) * HL : hh + HL];
+        // +x and -x are {o0, xo} in either order (integer sum)
+        const int hl = o0 + oth[hh + (p ? oxp1 : oxm0)] + up + dn;
         int s = own[hh];
-        const unsigned long long t = thr[(s < 0 ? 5 : 0) + ((hl + 4) >> 1)];
-        if (static_cast<unsigned long long>(w[k]) < t) {
+        const unsigned long long th = thr[(s < 0 ? 5 : 0) + ((hl + 4) >> 1)];
+        if (static_cast<unsigned long long>(w[k]) < th) {
           s = -s;
           own[hh] = static_cast<int8_t>(s);
           ++accepted;
@@ -69,11 +80,9 @@ __device__ __forceinline__ void ising_half_sweep(int L, int c, uint32_t sweep, u
           ms += s;
           if (kEnergy) eb += s * hl;
         }
-      }
-      ++hh;
-      if (++hx == HL) {
-        hx = 0;
-        ++y;
+        dn = o0;
+        o0 = up;
+        hh += HL;
       }
     }
   }
