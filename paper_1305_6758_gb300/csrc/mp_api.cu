@@ -318,6 +318,25 @@ int plan(mp_state* h, const mp_config* cfg) {
   const double target = cta_max <= 512 ? 16.0 : 8.0;
   MP_CUDA(h, reduce_prepare());
   std::vector<int> tp(n), slice(n), ring(n);
+  // The partial-sum ring (sweeps per half): the largest power of two up to 16
+  // among those that fit the most paths into one CTA -- shared memory, the
+  // CTA size and the named barriers permit (a shorter ring only flushes to
+  // the FP64 accumulators more often).
+  auto pick_ring = [&](int& r, int& sl, auto need, int threads) {
+    const int cap = std::max(1, threads > 32 ? std::min(15, cta_max / threads) : cta_max / threads);
+    int best_r = 0, best_sl = 0, best_fit = -1;
+    for (r = 16; r >= 1; r /= 2) {
+      const int s = need();
+      const int fit = s <= smem_max ? std::min(cap, smem_max / s) : 0;
+      if (fit > best_fit) {
+        best_fit = fit;
+        best_r = r;
+        best_sl = s;
+      }
+    }
+    r = best_r;
+    sl = best_sl;
+  };
   int max_tp = 32;
   for (int k = 0; k < n; ++k) {
     const int64_t N = sites_of(h->systems[k]);
@@ -335,11 +354,7 @@ int plan(mp_state* h, const mp_config* cfg) {
       auto need = [&]() {
         return round_up(slice_spin_offset(t, ring[k]) + 128 + 9 * half_plane_bytes(L, real), 128);
       };
-      slice[k] = need();
-      while (ring[k] > 1 && slice[k] > smem_max) {
-        ring[k] /= 2;
-        slice[k] = need();
-      }
+      pick_ring(ring[k], slice[k], need, t);
       if (slice[k] > smem_max)
         return fail(h, MP_EINVAL, "system %d: L=%d needs %d bytes of shared memory for its "
                     "half-plane ring (max %d)", k, L, slice[k], smem_max);
@@ -366,11 +381,9 @@ int plan(mp_state* h, const mp_config* cfg) {
     // partial-sum ring: the largest power of two up to 16 sweeps that fits
     ring[k] = 16;
     const int64_t lat = lattice_bytes(h->systems[k], real);
-    slice[k] = static_cast<int>(std::min<int64_t>(INT32_MAX / 2, round_up(slice_spin_offset(t, ring[k]) + lat, 128)));
-    while (ring[k] > 1 && slice[k] > smem_max) {
-      ring[k] /= 2;
-      slice[k] = static_cast<int>(std::min<int64_t>(INT32_MAX / 2, round_up(slice_spin_offset(t, ring[k]) + lat, 128)));
-    }
+    pick_ring(ring[k], slice[k], [&]() {
+      return static_cast<int>(std::min<int64_t>(INT32_MAX / 2, round_up(slice_spin_offset(t, ring[k]) + lat, 128)));
+    }, t);
     if (slice[k] > smem_max)
       return fail(h, MP_EINVAL, "system %d needs %d bytes of shared memory per path (max %d)", k,
                   slice[k], smem_max);
