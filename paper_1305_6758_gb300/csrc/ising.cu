@@ -50,8 +50,9 @@ __device__ __forceinline__ void ising_half_sweep(int L, int c, uint32_t sweep, u
                                                  int tid, int tp, int& accepted, int& eb, int& ms) {
   const int HL = L >> 1;
   const int strips = HL * ((L + 3) >> 2);
+  const PhiloxPrefix pre = philox_prefix(sweep, c2, c3, key);
   for (int t = tid; t < strips; t += tp) {
-    const Philox4 r = philox4x32_10(static_cast<uint32_t>(t), sweep, c2, c3, key);
+    const Philox4 r = philox4x32_10(static_cast<uint32_t>(t), pre, key);
     const uint32_t w[4] = {r.x, r.y, r.z, r.w};
     const int j = t / HL;
     const int hx = t - j * HL;

@@ -622,8 +622,9 @@ double calibrate(mp_state* h, int k) {
   p.records = h->d_rec;
   p.n_items = static_cast<int32_t>(sub.size());
   p.init_mode = h->init_mode | ((h->flags & MP_FLAG_TWO_START) ? kTwoStart : 0);
-  p.n_therm = sweeps - 1;
-  p.n_meas = 1;
+  // half thermalisation, half measurement sweeps, like a typical run
+  p.n_therm = sweeps / 2;
+  p.n_meas = sweeps - sweeps / 2;
   p.s_begin = 0;
   p.s_end = sweeps;
   p.key = philox_round_keys(h->seed);
@@ -700,7 +701,12 @@ int autotune(mp_state* h, const mp_config* cfg) {
     for (int t : cands) {
       h->tp_override[k] = t;
       if (plan(h, cfg) != MP_OK) continue;
-      const double rate = calibrate(h, k);
+      // the one-wave rate, times the fraction of the persistent grid's work
+      // the batch's items fill (few large items leave CTAs idle at the end)
+      const int64_t items = static_cast<int64_t>(h->items.size());
+      const int64_t waves = (items + h->grid - 1) / h->grid;
+      const double fill = waves > 0 ? static_cast<double>(items) / static_cast<double>(waves * h->grid) : 1.0;
+      const double rate = calibrate(h, k) * fill;
       if (rate > best) {
         best = rate;
         best_t = t;

@@ -56,4 +56,38 @@ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint3
   return Philox4{c0, c1, c2, c3};
 }
 
+// Round 1 of counters that differ only in word 0 (the site): the product of
+// word 2 and everything mixed with it depend on words 1..3 and the key alone,
+// so a loop over the sites of a sweep computes them once.
+struct PhiloxPrefix {
+  uint32_t x0, x1, c3k;
+};
+
+__device__ __forceinline__ PhiloxPrefix philox_prefix(uint32_t c1, uint32_t c2, uint32_t c3,
+                                                      const PhiloxKeys& key) {
+  const uint64_t pb = static_cast<uint64_t>(kPhiloxMulB) * c2;
+  return PhiloxPrefix{static_cast<uint32_t>(pb >> 32) ^ c1 ^ key.k0[0], static_cast<uint32_t>(pb),
+                      c3 ^ key.k1[0]};
+}
+
+// philox4x32_10(c0, c1, c2, c3, key) with round 1's fixed part precomputed.
+__device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, const PhiloxPrefix& pre,
+                                                 const PhiloxKeys& key) {
+  const uint64_t pa0 = static_cast<uint64_t>(kPhiloxMulA) * c0;
+  uint32_t x0 = pre.x0, x1 = pre.x1;
+  uint32_t x2 = static_cast<uint32_t>(pa0 >> 32) ^ pre.c3k, x3 = static_cast<uint32_t>(pa0);
+#pragma unroll
+  for (int round = 1; round < 10; ++round) {
+    const uint64_t pa = static_cast<uint64_t>(kPhiloxMulA) * x0;
+    const uint64_t pb = static_cast<uint64_t>(kPhiloxMulB) * x2;
+    const uint32_t n0 = static_cast<uint32_t>(pb >> 32) ^ x1 ^ key.k0[round];
+    const uint32_t n2 = static_cast<uint32_t>(pa >> 32) ^ x3 ^ key.k1[round];
+    x1 = static_cast<uint32_t>(pb);
+    x3 = static_cast<uint32_t>(pa);
+    x0 = n0;
+    x2 = n2;
+  }
+  return Philox4{x0, x1, x2, x3};
+}
+
 }  // namespace mpk

@@ -130,9 +130,9 @@ __global__ void __launch_bounds__(128) random_site_kernel(const SweepParams P, i
   int64_t accepted = 0;
   const int64_t S_total = P.n_therm + P.n_meas;
   for (int64_t s = 0; s < S_total; ++s) {
+    const PhiloxPrefix pre = philox_prefix(static_cast<uint32_t>(s), c2, kTagSite | sys_hi, P.key);
     for (int a = 0; a < N; ++a) {
-      const Philox4 r = philox4x32_10(static_cast<uint32_t>(a), static_cast<uint32_t>(s), c2,
-                                      kTagSite | sys_hi, P.key);
+      const Philox4 r = philox4x32_10(static_cast<uint32_t>(a), pre, P.key);
       const int i = static_cast<int>(((static_cast<uint64_t>(r.w) * 2u + 1u) *
                                       static_cast<uint64_t>(N)) >> 33);
       int nb[6];

@@ -252,12 +252,11 @@ struct SpinView {
 // given its local field (hx, hy, hz), Sec. 2.2: trial spin, energy change
 // from the local field, acceptance test.
 template <typename Real, bool kMeas, bool kEnergy>
-__device__ __forceinline__ void update(uint32_t i, uint32_t sweep, uint32_t c2, uint32_t c3,
-                                       const PhiloxKeys& key, const SpinView<Real>& own, int hh,
+__device__ __forceinline__ void update(uint32_t i, const PhiloxPrefix& pre, const PhiloxKeys& key, const SpinView<Real>& own, int hh,
                                        Real hx, Real hy, Real hz, Real J, Real hf, Real bp,
                                        int& accepted, Partials<Real>& part) {
   using A = Arith<Real>;
-  const Philox4 r = philox4x32_10(i, sweep, c2, c3, key);
+  const Philox4 r = philox4x32_10(i, pre, key);
   Real tx, ty, tz;
   A::trial(r.x, r.y, tx, ty, tz);
   const V3<Real> a = own.ld(hh);
@@ -281,8 +280,7 @@ __device__ __forceinline__ void update(uint32_t i, uint32_t sweep, uint32_t c2, 
 // One Metropolis attempt with the neighbours' half indices nb[0..nn) in `oth`,
 // summed in the fixed order nb[0], nb[1], ...
 template <typename Real, int NNB, bool kMeas, bool kEnergy>
-__device__ __forceinline__ void attempt(uint32_t i, uint32_t sweep, uint32_t c2, uint32_t c3,
-                                        const PhiloxKeys& key, const SpinView<Real>& own,
+__device__ __forceinline__ void attempt(uint32_t i, const PhiloxPrefix& pre, const PhiloxKeys& key, const SpinView<Real>& own,
                                         const SpinView<Real>& oth, int hh, const int* nb, int nn,
                                         Real J, Real hf, Real bp, int& accepted,
                                         Partials<Real>& part) {
@@ -291,7 +289,7 @@ __device__ __forceinline__ void attempt(uint32_t i, uint32_t sweep, uint32_t c2,
   for (int j = 0; j < NNB; ++j) {
     if (j < nn) f = add3(f, oth.ld(nb[j]));
   }
-  update<Real, kMeas, kEnergy>(i, sweep, c2, c3, key, own, hh, f.x, f.y, f.z, J, hf, bp, accepted,
+  update<Real, kMeas, kEnergy>(i, pre, key, own, hh, f.x, f.y, f.z, J, hf, bp, accepted,
                                part);
 }
 
@@ -318,8 +316,8 @@ constexpr int kColumnUnroll = sizeof(Real) == 8 ? 1 : 4;
 // order (a + b = b + a exactly), so the sum keeps the fixed order +x, -x, +y,
 // -y, +z, -z.  K = 0: every site decoded from its half index (open chains).
 template <typename Real, class Geom, bool kMeas, bool kEnergy>
-__device__ __forceinline__ void half_sweep(const Geom& geo, int c, uint32_t sweep, uint32_t c2,
-                                           uint32_t c3, const PhiloxKeys& key, Real* sp, int tid,
+__device__ __forceinline__ void half_sweep(const Geom& geo, int c, const PhiloxPrefix& pre,
+                                           const PhiloxKeys& key, Real* sp, int tid,
                                            int tp, int K, Real J, Real hf, Real bp,
                                            int& accepted, Partials<Real>& part) {
   const int S = geo.stride();
@@ -349,7 +347,7 @@ __device__ __forceinline__ void half_sweep(const Geom& geo, int c, uint32_t swee
           const V3<Real> cz = oth.ld(z == LL - 1 ? hh - (LL - 1) * HP : hh + HP);
           const V3<Real> f =
               add3(add3(add3(add3(add3(o0, oth.ld(nxo)), oth.ld(hh + oyp)), oth.ld(hh + oym)), cz), mz);
-          update<Real, kMeas, kEnergy>(static_cast<uint32_t>(2 * hh + p), sweep, c2, c3, key, own, hh,
+          update<Real, kMeas, kEnergy>(static_cast<uint32_t>(2 * hh + p), pre, key, own, hh,
                                        f.x, f.y, f.z, J, hf, bp, accepted, part);
           mz = o0;
           o0 = cz;
@@ -363,7 +361,7 @@ __device__ __forceinline__ void half_sweep(const Geom& geo, int c, uint32_t swee
     int nb[Geom::NNB];
     int nn;
     const int i = geo.site(hh, c, nb, nn);
-    attempt<Real, Geom::NNB, kMeas, kEnergy>(static_cast<uint32_t>(i), sweep, c2, c3, key, own, oth,
+    attempt<Real, Geom::NNB, kMeas, kEnergy>(static_cast<uint32_t>(i), pre, key, own, oth,
                                              hh, nb, nn, J, hf, bp, accepted, part);
   }
 }
@@ -615,17 +613,18 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
   bool canceled = false;
   for (int64_t s = P.s_begin; s < P.s_end; ++s) {
     const uint32_t sw = static_cast<uint32_t>(s);
+    const PhiloxPrefix pre = philox_prefix(sw, c2, c3u, P.key);
     Partials<Real> part{Real(0), Real(0), Real(0), Real(0)};
     poll_cancel(P, s, tid, &cancel_flag[gidx]);
     if (s < P.n_therm) {
-      half_sweep<Real, Geom, false, false>(geo, 0, sw, c2, c3u, P.key, sp, tid, tp, K, J, hf,
+      half_sweep<Real, Geom, false, false>(geo, 0, pre, P.key, sp, tid, tp, K, J, hf,
                                            bp, accepted, part);
       group_sync(tp, bar);
       if (cancel_flag[gidx]) {
         canceled = true;
         break;
       }
-      half_sweep<Real, Geom, false, false>(geo, 1, sw, c2, c3u, P.key, sp, tid, tp, K, J, hf,
+      half_sweep<Real, Geom, false, false>(geo, 1, pre, P.key, sp, tid, tp, K, J, hf,
                                            bp, accepted, part);
       group_sync(tp, bar);
       continue;
@@ -633,7 +632,7 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
     // Measurement sweep j.  Colour-0 sites keep their values during the
     // colour-1 pass, so the colour-1 local fields give every bond once.
     const int64_t j = s - P.n_therm;
-    half_sweep<Real, Geom, true, false>(geo, 0, sw, c2, c3u, P.key, sp, tid, tp, K, J, hf, bp,
+    half_sweep<Real, Geom, true, false>(geo, 0, pre, P.key, sp, tid, tp, K, J, hf, bp,
                                         accepted, part);
     group_sync(tp, bar);
     if (cancel_flag[gidx]) {
@@ -641,7 +640,7 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
       break;
     }
     meter.maybe_flush(j);
-    half_sweep<Real, Geom, true, true>(geo, 1, sw, c2, c3u, P.key, sp, tid, tp, K, J, hf, bp,
+    half_sweep<Real, Geom, true, true>(geo, 1, pre, P.key, sp, tid, tp, K, J, hf, bp,
                                        accepted, part);
     meter.record(j, part);
     group_sync(tp, bar);
@@ -875,6 +874,7 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
 
   for (int64_t s = P.s_begin; s < P.s_end && ok; ++s) {
     const uint32_t sw = static_cast<uint32_t>(s);
+    const PhiloxPrefix pre = philox_prefix(sw, c2, c3u, P.key);
     const bool meas = s >= P.n_therm;
     const int64_t j = s - P.n_therm;
     Partials<Real> part{Real(0), Real(0), Real(0), Real(0)};
@@ -933,13 +933,13 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
         const uint32_t i = static_cast<uint32_t>(2 * (hp + HP * z) + p);
         if (meas) {
           if (energy)
-            update<Real, true, true>(i, sw, c2, c3u, P.key, own, hp, f.x, f.y, f.z, J, hf, bp,
+            update<Real, true, true>(i, pre, P.key, own, hp, f.x, f.y, f.z, J, hf, bp,
                                      accepted, part);
           else
-            update<Real, true, false>(i, sw, c2, c3u, P.key, own, hp, f.x, f.y, f.z, J, hf, bp,
+            update<Real, true, false>(i, pre, P.key, own, hp, f.x, f.y, f.z, J, hf, bp,
                                       accepted, part);
         } else {
-          update<Real, false, false>(i, sw, c2, c3u, P.key, own, hp, f.x, f.y, f.z, J, hf, bp,
+          update<Real, false, false>(i, pre, P.key, own, hp, f.x, f.y, f.z, J, hf, bp,
                                      accepted, part);
         }
       };
