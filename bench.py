@@ -115,13 +115,13 @@ BYTES_PER_ATTEMPT_FP32 = 24
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the dominant kernel, from ncu captures of the kernels built from the sources
 # with this hash (sha256 over csrc/, first 16 hex digits); any change of the
-# sources voids it and the roofline reports traffic null.  sc16: the timed
-# launch of the default command, captured at full size (one ncu pass).  large:
-# a 10 + 10-sweep capture, 18.7 GB one-off (initial state, read-out) plus
-# 19.33 GB per sweep, scaled to 500 + 1000 sweeps.
+# sources voids it and the roofline reports traffic null.  Both are the timed
+# launch of the workload's bench command, captured at full size (one ncu pass):
+# sc16 reads 0.68 MB (tables; the lattices stay in shared memory), large moves
+# 28.97 TB against 28.99 TB of algorithmic bytes.
 TRAFFIC = {
-    "sc16": {"sources": "ca96ac9ef8977eaf", "bytes": 0.679e6},
-    "large": {"sources": "ca96ac9ef8977eaf", "bytes": 18.7e9 + 1500 * 19.327e9},
+    "sc16": {"sources": "8848ab6bcde0d4dc", "bytes": 0.683e6},
+    "large": {"sources": "8848ab6bcde0d4dc", "bytes": 14.47e12 + 14.50e12},
 }
 
 
