@@ -80,7 +80,12 @@ extern "C" {
                                  each system in the batch's own kernel (one
                                  wave of its work items, ~2e8 attempts each)
                                  and keep the fastest; ignored when
-                                 threads_per_path is set */
+                                 threads_per_path is set.  The choice is
+                                 remembered for the life of the process: a
+                                 later create of a batch of the same shape
+                                 (device, precision, init mode, cta_threads,
+                                 and per system lattice, L, n_paths) on the
+                                 same device takes it without timing */
 #define MP_FLAG_TWO_START 16u /* Sec. 4's convergence check: in every system the
                                  first ceil(P/2) paths start from init_mode, the
                                  other floor(P/2) from the ordered state; the

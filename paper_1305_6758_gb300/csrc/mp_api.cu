@@ -12,6 +12,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -678,10 +680,35 @@ std::vector<int> tp_candidates(mp_state* h, int k, int cta_max) {
   return c;
 }
 
+// The autotuner's choices, remembered for the life of the process: a later
+// handle whose batch has the same shape on the same device (the key below)
+// takes the measured layout without timing it again.  Temperatures, fields
+// and seeds are not part of the key: they do not change the launch shape.
+std::mutex g_tune_mu;
+std::map<std::string, std::vector<int>> g_tune_memo;
+
+std::string tune_key(const mp_state* h, const mp_config* cfg) {
+  std::string k = std::to_string(h->device) + "/" + std::to_string(h->precision) + "/" +
+                  std::to_string(h->flags & (MP_FLAG_STREAM | MP_FLAG_TWO_START)) + "/" +
+                  std::to_string(h->init_mode) + "/" + std::to_string(cfg->cta_threads);
+  for (const mp_system& s : h->systems)
+    k += "/" + std::to_string(s.lattice) + ":" + std::to_string(s.L) + ":" + std::to_string(s.n_paths);
+  return k;
+}
+
 // Pick each system's threads per path by measuring the candidates in the
 // batch's own kernel; leaves the handle planned with the choice.
 int autotune(mp_state* h, const mp_config* cfg) {
   const int n = static_cast<int>(h->systems.size());
+  const std::string key = tune_key(h, cfg);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_memo.find(key);
+    if (it != g_tune_memo.end() && static_cast<int>(it->second.size()) == n) {
+      h->tp_override = it->second;
+      return plan(h, cfg);
+    }
+  }
   h->tp_override.assign(n, 0);
   int smem_max = 0, cta_max = 0;
   MP_CUDA(h, sweep_prepare(h->precision, h->variant, h->device, &smem_max, &cta_max));
@@ -715,7 +742,12 @@ int autotune(mp_state* h, const mp_config* cfg) {
     h->tp_override[k] = best_t;
   }
   h->err.clear();
-  return plan(h, cfg);
+  const int rc = plan(h, cfg);
+  if (rc == MP_OK) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_memo[key] = h->tp_override;
+  }
+  return rc;
 }
 
 // After the stream has drained: MP_ETIMEOUT if a kernel's bounded wait gave up.

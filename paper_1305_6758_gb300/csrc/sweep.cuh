@@ -139,9 +139,12 @@ struct Arith<double> {
 // Periodic simple cubic lattice with compile-time L (even).  site() returns
 // the site index of half index h in colour c and fills the half indices of
 // its neighbours in the other colour, in the fixed order +x, -x, +y, -y, +z, -z.
-// Half index h = hx + HL*y + HP*z with hx = x / 2.
-template <int L>
+// Half index h = hx + HL*y + HP*z with hx = x / 2.  kMixed: the geometry as
+// run by the mixed-size kernel (which takes the column-walk chunks of
+// column_chunk_fp32(L, true)).
+template <int L, bool kMixed = false>
 struct GeomSC {
+  static constexpr bool kInMixed = kMixed;
   static constexpr int N = L * L * L;
   static constexpr int NH = N / 2;
   static constexpr int HL = L / 2;
@@ -293,13 +296,31 @@ __device__ __forceinline__ void attempt(uint32_t i, const PhiloxPrefix& pre, con
                                part);
 }
 
-// Sites of a column segment interleaved by the compiler (independent Philox
-// chains) in the FP32 kernels (512-thread CTAs, up to 128 registers per
-// thread): 8 for L = 16, whose benchmark layout walks whole 16-plane columns,
-// 4 otherwise (measured: 8 everywhere loses 3-12% on the shorter segments of
-// other sizes, 16 spills).
-template <typename Real, int L>
-constexpr int kColumnUnroll = sizeof(Real) == 8 ? 1 : (L == 16 ? 8 : 4);
+// Planes of a column segment interleaved by the compiler (independent Philox
+// chains), the chunk U: every segment is a whole number of chunks (the
+// segment count K is restricted to divisors of L whose segment length L/K is
+// a multiple of U), so no site is left to a serial remainder loop.  FP32
+// kernels (512-thread CTAs, up to 128 registers per thread): 8 for L = 16,
+// 6 for 12, 18 and 24, 4 for 8 and 20, 7 for 14, 3 for 6, 2 for 10, 22 and 26,
+// 1 for 2 and 4 (whose columns are too short to split into chunks).  The
+// mixed-size kernel holds every size's walk in one register allocation and
+// takes 3 for 12, 18, 24 and 2 for 14, which keep it within 128 registers
+// without spills.  FP64 kernels (64 registers per thread) take one site at a
+// time.  Measured on the benchmark layouts: chunks of 2 lose 6% against 4, 8
+// gains 1% over 4 at L = 16, 16 spills; whole chunks of 6 gain 6-8% over a
+// runtime unroll of 4 at L = 12, 18, 24.
+constexpr int column_chunk_fp32(int L, bool mixed) {
+  return L == 16                   ? 8
+         : (L % 6 == 0 && L >= 12) ? (mixed ? 3 : 6)
+         : (L == 8 || L == 20)     ? 4
+         : L == 14                 ? (mixed ? 2 : 7)
+         : L == 6                  ? 3
+         : L <= 4                  ? 1
+                                   : 2;
+}
+template <typename Real, class Geom>
+constexpr int kColumnChunk =
+    sizeof(Real) == 8 ? 1 : column_chunk_fp32(2 * Geom::HL, Geom::kInMixed);
 
 // One half-sweep of one thread: every site of colour c it owns.
 //
@@ -309,7 +330,8 @@ constexpr int kColumnUnroll = sizeof(Real) == 8 ? 1 : (L == 16 ? 8 : 4);
 // (column col, segment g), numbered u = g * HP + col, are dealt out to the
 // threads round by round (thread tid takes u = tid, tid + tp, ...), so the
 // lanes of a warp work on consecutive columns of the same planes and their
-// shared-memory accesses are consecutive elements.  Within a segment the +-x
+// shared-memory accesses are consecutive elements.  A segment is walked in
+// chunks of kColumnChunk planes whose sites the compiler interleaves.  Within a segment the +-x
 // and +-y neighbour offsets are fixed, and since the x parity flips from
 // plane to plane, the other colour's spin at the site's own half index is
 // both an x neighbour of the site in plane z and the -z neighbour of the site
@@ -340,10 +362,15 @@ __device__ __forceinline__ void half_sweep(const Geom& geo, int c, const PhiloxP
         const int oym = (y == 0) ? (LL - 1) * HL : -HL;
         const int oxp1 = (hx == HL - 1) ? -(HL - 1) : 1;  // +x offset when x is odd
         const int oxm0 = (hx == 0) ? (HL - 1) : -1;         // -x offset when x is even
+        constexpr int U = kColumnChunk<Real, Geom>;
         int hh = col + HP * z0;
         V3<Real> o0 = oth.ld(hh);  // the other colour at the site's half index
         V3<Real> mz = oth.ld(z0 == 0 ? hh + (LL - 1) * HP : hh - HP);  // -z neighbour
-#pragma unroll(kColumnUnroll<Real, LL>)
+        // segments are whole chunks: with that hint the compiler leaves out the
+        // remainder loop; at L = 16 (chunks of 8) the kernel fits 128
+        // registers without spills only without it
+        if constexpr (U != 8) __builtin_assume(seg % U == 0);
+#pragma unroll(U)
         for (int z = z0; z < z0 + seg; ++z, hh += HP) {
           const int p = (y + z + c) & 1;
           const int nxo = hh + (p ? oxp1 : oxm0);
@@ -562,15 +589,18 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
   const int init = path_init_mode(P.init_mode, path, sy.n_paths);
   const Real J = static_cast<Real>(sy.J), hf = static_cast<Real>(sy.h);
   const Real bp = A::beta_param(sy.beta);
-  // column segments per column: the divisor K of L that spreads the HP * K
-  // units most evenly over the tp threads (the smallest such K, for the
-  // longest segments); 0 = decode every site (open chains)
+  // column segments per column: the divisor K of L, with segments of whole
+  // chunks, that spreads the HP * K units most evenly over the tp threads
+  // (the smallest such K, for the longest segments); 0 = decode every site
+  // (open chains)
   int K = 0;
   if constexpr (Geom::kColumns) {
     constexpr int LL = 2 * Geom::HL;
+    constexpr int U = kColumnChunk<Real, Geom>;
+    static_assert(LL % U == 0, "a whole column is a whole number of chunks");
     double best = -1.0;
     for (int k = 1; k <= LL; ++k) {
-      if (LL % k) continue;
+      if (LL % k || (LL / k) % U) continue;
       const int units = Geom::HP * k;
       const double eff = static_cast<double>(units) / (static_cast<double>((units + tp - 1) / tp) * tp);
       if (eff > best + 1e-9) {

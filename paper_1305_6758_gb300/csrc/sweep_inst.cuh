@@ -28,7 +28,7 @@ __device__ __forceinline__ void dispatch_path(const DevSystem& sy, int sys_idx, 
     switch (sy.L) {
 #define MPK_CASE(LL)                                                           \
   case LL:                                                                     \
-    run_path<Real>(GeomSC<LL>{}, sy, sys_idx, path, P, slice, tid, tp, bar);   \
+    run_path<Real>(GeomSC<LL, true>{}, sy, sys_idx, path, P, slice, tid, tp, bar); \
     break;
       MPK_FOR_EACH_L(MPK_CASE)
 #undef MPK_CASE

@@ -56,6 +56,25 @@ def test_split_schedule_with_checkpoint_equals_one_run(precision, tol):
         np.testing.assert_allclose(f[:, FIELDS], r[:, FIELDS], rtol=0, atol=tol)
 
 
+def test_ising_split_schedule_equals_one_run():
+    """The same for the Appendix A kernel: spins are bytes, the trajectories
+    integer, so the records agree up to the order of the FP64 sums."""
+    systems = [mp.System(12, 2.2, n_paths=9, lattice=mp.ISING), mp.System(6, 1.5, h=0.2, n_paths=5, lattice=mp.ISING)]
+    with mp.Simulation(systems, 4, 6, seed=8) as whole:
+        whole.run_sweeps(10)
+        ref = [whole.paths(k) for k in range(2)]
+    with mp.Simulation(systems, 4, 6, seed=8) as a:
+        a.run_sweeps(5)
+        blob = a.checkpoint()
+    with mp.Simulation(systems, 4, 6, seed=8) as b:
+        b.restore(blob)
+        b.run_sweeps(5)
+        got = [b.paths(k) for k in range(2)]
+    for r, g in zip(ref, got):
+        np.testing.assert_allclose(g[:, FIELDS], r[:, FIELDS], rtol=1e-12, atol=1e-12)
+        np.testing.assert_array_equal(g[:, 17], r[:, 17])
+
+
 def test_checkpoint_errors():
     with mp.Simulation(SYSTEMS, 2, 2) as a:
         with pytest.raises(mp.MPError) as ei:

@@ -141,3 +141,20 @@ def test_autotune_changes_only_the_launch_shape():
         shapes = [sim.system_plan(k) for k in range(3)]
     assert shapes[2]["streamed"] and not shapes[0]["streamed"]
     assert all(s["threads_per_path"] % 32 == 0 for s in shapes)
+
+
+def test_autotune_choice_is_remembered_for_the_same_batch_shape():
+    """A second handle of the same batch shape takes the first one's measured
+    layout (no timing at create); another temperature does not change the key."""
+    import time
+    systems = [mp.System(10, 1.3, n_paths=700), mp.System(14, 0.9, n_paths=90)]
+    t0 = time.perf_counter()
+    with mp.Simulation(systems, 1, 1, flags=mp.FLAG_AUTOTUNE, seed=3) as a:
+        first = [a.system_plan(k) for k in range(2)], a.plan()
+    t1 = time.perf_counter()
+    hot = [mp.System(10, 2.0, n_paths=700), mp.System(14, 1.1, n_paths=90)]
+    with mp.Simulation(hot, 1, 1, flags=mp.FLAG_AUTOTUNE, seed=4) as b:
+        again = [b.system_plan(k) for k in range(2)], b.plan()
+    t2 = time.perf_counter()
+    assert again == first
+    assert t2 - t1 < t1 - t0
