@@ -47,7 +47,7 @@ TEMPS21 = [0.5 + 2.0 * k / 20 for k in range(21)]
 WORKLOADS = {
     "sc16": dict(
         systems=[(16, T, 4096) for T in TEMPS21], n_therm=2000, n_meas=2000, precision="fp32",
-        bound="alu", cpu_paths=2, ref_paths=1, fp64_paths=64,
+        bound="alu", cpu_paths=6, ref_paths=1, fp64_paths=64,
         text=("simple cubic L=16 periodic, J=1, h=0, 21 temperatures in [0.5,2.5], 4096 paths per "
               "temperature, 2000+2000 checkerboard sweeps, FP32 spins in shared memory, FP64 "
               "accumulators and reduction")),
@@ -115,13 +115,15 @@ BYTES_PER_ATTEMPT_FP32 = 24
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the dominant kernel, from ncu captures of the kernels built from the sources
 # with this hash (sha256 over csrc/, first 16 hex digits); any change of the
-# sources voids it and the roofline reports traffic null.  Both are the timed
+# sources voids it and the roofline reports traffic null.  Each is the timed
 # launch of the workload's bench command, captured at full size (one ncu pass):
-# sc16 reads 0.68 MB (tables; the lattices stay in shared memory), large moves
-# 28.97 TB against 28.99 TB of algorithmic bytes.
+# sc16 reads 0.81 MB (tables; the lattices stay in shared memory), large moves
+# 28.96 TB against 28.99 TB of algorithmic bytes, batched 340 GB (its streamed
+# L = 32 lattices, 402 GB algorithmic, partly served from L2).
 TRAFFIC = {
-    "sc16": {"sources": "8848ab6bcde0d4dc", "bytes": 0.683e6},
-    "large": {"sources": "8848ab6bcde0d4dc", "bytes": 14.47e12 + 14.50e12},
+    "sc16": {"sources": "8ab0f37cd01fc591", "bytes": 0.814e6},
+    "large": {"sources": "8ab0f37cd01fc591", "bytes": 14.46e12 + 14.50e12},
+    "batched": {"sources": "8ab0f37cd01fc591", "bytes": 142.92e9 + 197.19e9},
 }
 
 
@@ -437,7 +439,8 @@ def main():
             "config": {"workload": w["text"], "name": args.workload, "n_therm": n_therm, "n_meas": n_meas,
                        "systems": len(systems), "paths": paths_rank, "parallelism": f"replicas x{world}",
                        "l2": "flushed between timed steps (256 MB write)", "plan": sim.plan(),
-                       "autotuned": [sim.system_plan(k) for k in sorted({0, n_sys // 2, n_sys - 1})]},
+                       "autotuned": [sim.system_plan(k) for k in
+                                     (range(n_sys) if n_sys <= 8 else sorted({0, n_sys // 2, n_sys - 1}))]},
             "paths_per_s": paths_per_s,
             "sigma": {"e_se_max": max(e["e_se"] for e in ests), "m_se_max": max(e["m_se"] for e in ests),
                       "e": [[e["T"], e["e"], e["e_se"]] for e in ests[:: max(1, n_sys // 3)]]},
