@@ -117,13 +117,13 @@ BYTES_PER_ATTEMPT_FP32 = 24
 # with this hash (sha256 over csrc/, first 16 hex digits); any change of the
 # sources voids it and the roofline reports traffic null.  Each is the timed
 # launch of the workload's bench command, captured at full size (one ncu pass):
-# sc16 reads 0.81 MB (tables; the lattices stay in shared memory), large moves
-# 28.96 TB against 28.99 TB of algorithmic bytes, batched 340 GB (its streamed
+# sc16 reads 0.75 MB (tables; the lattices stay in shared memory), large moves
+# 28.94 TB against 28.99 TB of algorithmic bytes, batched 328 GB (its streamed
 # L = 32 lattices, 402 GB algorithmic, partly served from L2).
 TRAFFIC = {
-    "sc16": {"sources": "8ab0f37cd01fc591", "bytes": 0.814e6},
-    "large": {"sources": "8ab0f37cd01fc591", "bytes": 14.46e12 + 14.50e12},
-    "batched": {"sources": "8ab0f37cd01fc591", "bytes": 142.92e9 + 197.19e9},
+    "sc16": {"sources": "1353bf33dc85ee14", "bytes": 0.746e6},
+    "large": {"sources": "1353bf33dc85ee14", "bytes": 14.44e12 + 14.50e12},
+    "batched": {"sources": "1353bf33dc85ee14", "bytes": 129.70e9 + 198.21e9},
 }
 
 

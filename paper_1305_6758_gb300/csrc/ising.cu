@@ -100,10 +100,11 @@ __device__ void run_path_ising(const DevSystem& sy, int sys_idx, int64_t path,
   const uint32_t sys_hi = static_cast<uint32_t>(sys_idx) << 8;
   const int init = path_init_mode(P.init_mode, path, sy.n_paths);
   const int64_t j_first = P.s_begin > P.n_therm ? P.s_begin - P.n_therm : 0;
-  const Meter<double> meter{reinterpret_cast<double*>(slice + slice_acc_offset()),
-                            reinterpret_cast<double*>(slice + slice_red_offset()),
-                            sy.ring, tp >> 5, tid & 31, tid >> 5, tid,
-                            1.0 / static_cast<double>(N), sy.J, sy.h, j_first};
+  Meter<double> meter{reinterpret_cast<double*>(slice + slice_acc_offset()),
+                      reinterpret_cast<double*>(slice + slice_red_offset()),
+                      sy.ring, tp >> 5, tid & 31, tid >> 5, tid,
+                      1.0 / static_cast<double>(N), sy.J, sy.h, j_first};
+  meter.start();
   unsigned char* st = path_state(P, sys_idx, path);
   int8_t* st_spins = st ? reinterpret_cast<int8_t*>(st + kStateHeader) : nullptr;
   __shared__ int cancel_flag[kMaxGroups];
@@ -164,12 +165,13 @@ __device__ void run_path_ising(const DevSystem& sy, int sys_idx, int64_t path,
       ms += __shfl_xor_sync(0xffffffffu, ms, o);
     }
     if ((tid & 31) == 0) {
-      double* r = meter.slot(j) + (tid >> 5) * kRedSlots;
+      double* r = meter.cur_slot() + (tid >> 5) * kRedSlots;
       r[0] = static_cast<double>(eb);
       r[1] = 0.0;
       r[2] = 0.0;
       r[3] = static_cast<double>(ms);
     }
+    meter.advance();
     group_sync(tp, bar);
   }
   if (canceled) {

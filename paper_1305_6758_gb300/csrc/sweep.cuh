@@ -411,9 +411,18 @@ struct Meter {
   double invN;
   Real J, hf;
   int64_t j_first;  // first measurement sweep of this call (earlier ones are already flushed)
+  // ring slot of the next measurement sweep j to record, ((j / R) & 1) * R +
+  // j % R, kept in a 32-bit counter that advances one sweep at a time (no
+  // 64-bit division per sweep); start() sets it for j_first
+  int cur = 0;
 
+  __device__ void start() { cur = static_cast<int>(((j_first / R) & 1) * R + j_first % R); }
   __device__ Real* slot(int64_t j) const {
     return red + ((((j / R) & 1) * R + (j % R)) * nwarps) * kRedSlots;
+  }
+  __device__ Real* cur_slot() const { return red + (cur * nwarps) * kRedSlots; }
+  __device__ void advance() {
+    if (++cur == 2 * R) cur = 0;
   }
   // Per-site observables (Sec. 2.2) of one measurement sweep from its slot.
   __device__ void observe(const Real* sl, Real& e, Real& ex, Real& ey, Real& ez) const {
@@ -430,8 +439,9 @@ struct Meter {
     ey = MY * rN;
     ez = MZ * rN;
   }
-  // Store this warp's partials of measurement sweep j (every lane calls).
-  __device__ void record(int64_t j, Partials<Real> part) const {
+  // Store this warp's partials of the current measurement sweep and move to
+  // the next (every lane calls, once per measurement sweep, in order).
+  __device__ void record(Partials<Real> part) {
     using A = Arith<Real>;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -441,12 +451,13 @@ struct Meter {
       part.mz += A::shfl(part.mz, o);
     }
     if (lane == 0) {
-      Real* r = slot(j) + warp * kRedSlots;
+      Real* r = cur_slot() + warp * kRedSlots;
       r[0] = part.eb;
       r[1] = part.mx;
       r[2] = part.my;
       r[3] = part.mz;
     }
+    advance();
   }
   // Flush sweeps j0 .. j0+n-1 (one ring half): lane l takes sweep j0+l; warp
   // w owns observables w, w + warps, ...; each owned observable is summed
@@ -482,9 +493,10 @@ struct Meter {
       if (lane == 0) acc[k] += static_cast<double>(v);
     }
   }
-  // At measurement sweep j, after its first barrier: flush the previous half.
+  // At measurement sweep j (the current one), after its first barrier: flush
+  // the previous half.
   __device__ void maybe_flush(int64_t j) const {
-    if (j > j_first && (j % R) == 0) {
+    if ((cur == 0 || cur == R) && j > j_first) {
       const int64_t j0 = j - R > j_first ? j - R : j_first;
       flush(j0, static_cast<int>(j - j0));
     }
@@ -610,10 +622,11 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
     }
   }
   const int64_t j_first = P.s_begin > P.n_therm ? P.s_begin - P.n_therm : 0;
-  const Meter<Real> meter{reinterpret_cast<double*>(slice + slice_acc_offset()),
-                          reinterpret_cast<Real*>(slice + slice_red_offset()),
-                          sy.ring, tp >> 5, tid & 31, tid >> 5, tid,
-                          1.0 / static_cast<double>(sy.N), J, hf, j_first};
+  Meter<Real> meter{reinterpret_cast<double*>(slice + slice_acc_offset()),
+                    reinterpret_cast<Real*>(slice + slice_red_offset()),
+                    sy.ring, tp >> 5, tid & 31, tid >> 5, tid,
+                    1.0 / static_cast<double>(sy.N), J, hf, j_first};
+  meter.start();
   unsigned char* st = path_state(P, sys_idx, path);
   Real* st_spins = st ? reinterpret_cast<Real*>(st + kStateHeader) : nullptr;
   __shared__ int cancel_flag[kMaxGroups];
@@ -675,7 +688,7 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
     meter.maybe_flush(j);
     half_sweep<Real, Geom, true, true>(geo, 1, pre, P.key, sp, tid, tp, K, J, hf, bp,
                                        accepted, part);
-    meter.record(j, part);
+    meter.record(part);
     group_sync(tp, bar);
   }
   if (canceled) {  // the call is discarded: no record, no saved state
@@ -856,10 +869,11 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
   const Real J = static_cast<Real>(sy.J), hf = static_cast<Real>(sy.h);
   const Real bp = A::beta_param(sy.beta);
   const int64_t j_first = P.s_begin > P.n_therm ? P.s_begin - P.n_therm : 0;
-  const Meter<Real> meter{reinterpret_cast<double*>(slice + slice_acc_offset()),
-                          reinterpret_cast<Real*>(slice + slice_red_offset()),
-                          sy.ring, tp >> 5, tid & 31, tid >> 5, tid,
-                          1.0 / static_cast<double>(sy.N), J, hf, j_first};
+  Meter<Real> meter{reinterpret_cast<double*>(slice + slice_acc_offset()),
+                    reinterpret_cast<Real*>(slice + slice_red_offset()),
+                    sy.ring, tp >> 5, tid & 31, tid >> 5, tid,
+                    1.0 / static_cast<double>(sy.N), J, hf, j_first};
+  meter.start();
   __shared__ int abort_flag[kMaxGroups];  // per thread group: a bounded wait gave up, or canceled
   const int gidx = bar - 1;
   const bool producer = tid == 0;
@@ -1021,7 +1035,7 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
     }
     if (!ok) break;
     if (meas) {
-      meter.record(j, part);
+      meter.record(part);
       group_sync(tp, bar);
     }
   }
