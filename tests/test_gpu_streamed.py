@@ -158,3 +158,36 @@ def test_autotune_choice_is_remembered_for_the_same_batch_shape():
     t2 = time.perf_counter()
     assert again == first
     assert t2 - t1 < t1 - t0
+
+
+def test_fp32_batched_form_against_the_oracle():
+    """The batched workload's shape in FP32: uneven sizes in one persistent
+    launch, L = 32 streamed, autotuned. Every system's <e> and <|m|> are
+    within 3 combined standard errors of the FP64 oracle, and <e> is within
+    1e-4 (plus 3 standard errors) of the FP64 GPU form from the same starts."""
+    sizes = ((8, 512), (12, 256), (16, 128), (20, 64), (24, 32), (32, 16))
+    systems = [mp.System(L, 1.44, n_paths=P) for L, P in sizes]
+    with mp.Simulation(systems, 100, 100, seed=11, flags=mp.FLAG_AUTOTUNE) as sim:
+        sim.run()
+        e32 = [sim.estimates(k) for k in range(len(systems))]
+    with mp.Simulation(systems, 100, 100, seed=11, precision=mp.FP64) as sim:
+        sim.run()
+        e64 = [sim.estimates(k) for k in range(len(systems))]
+    orc = O.run([O.System(L, 1.44, n_paths=P, path_count=min(P, 48)) for L, P in sizes], 100, 100, seed=11)
+    for k, (L, _) in enumerate(sizes):
+        ref = O.estimates(orc[k], L ** 3, 1.44)
+        for key in ("e", "m"):
+            z = abs(e32[k][key] - ref[key]) / np.hypot(e32[k][key + "_se"], ref[key + "_se"])
+            assert z < 3, (L, key, e32[k][key], ref[key], z)
+        assert abs(e32[k]["e"] - e64[k]["e"]) < 1e-4 + 3 * e32[k]["e_se"], (L, e32[k]["e"], e64[k]["e"])
+
+
+@pytest.mark.parametrize("L", [12, 24])
+def test_fp32_mixed_kernel_follows_the_single_size_kernel(L):
+    """The mixed-size kernel walks L = 12 and 24 in chunks of 3 planes, the
+    kernels compiled for one size in chunks of 6: the per-site arithmetic is
+    the same, so the records agree to the rounding of FP32 partial sums."""
+    alone = [mp.System(L, 1.2, n_paths=5)]
+    a, _ = gpu_records(alone, 3, 4, seed=12)
+    b, _ = gpu_records(alone + [mp.System(8, 1.0, n_paths=7)], 3, 4, seed=12)
+    np.testing.assert_allclose(b[0][:, FIELDS], a[0][:, FIELDS], rtol=2e-6, atol=2e-7)
