@@ -182,12 +182,20 @@ def test_free_spins_in_field():
 
 
 def test_infinite_temperature():
+    """beta -> 0: every spin is a fresh uniform direction each sweep, so the
+    moments are those of N independent unit vectors.  With 3N distinct bonds
+    (L = 4), <e^2> = 3N (1/3) / N^2 = 1/N; <|m|^4> = (5N^2 - 2N) / (3N^4),
+    hence U_L = 1 - <|m|^4> / (3 <|m|^2>^2) = 4/9 + 2/(9N)."""
+    N = 64
     rec = O.run([O.System(L=4, T=1e12, n_paths=512)], 2, 50)[0]
-    est = O.estimates(rec, 64, 1e12)
+    est = O.estimates(rec, N, 1e12)
     assert est["acc"] == 1.0  # every move is accepted at beta -> 0
     assert zdiff(est["e"], 0.0, est["e_se"]) < 4
-    assert zdiff(est["m2"], 1.0 / 64, est["m2_se"]) < 4  # <|m|^2> = 1/N for iid spins
+    assert zdiff(est["m2"], 1.0 / N, est["m2_se"]) < 4  # <|m|^2> = 1/N for iid spins
     assert zdiff(est["mx"], 0.0, est["mx_se"]) < 4
+    assert zdiff(est["e2"], 1.0 / N, est["e2_se"]) < 4
+    assert zdiff(est["m4"], (5.0 * N * N - 2.0 * N) / (3.0 * N ** 4), est["m4_se"]) < 4
+    assert zdiff(est["binder"], 4.0 / 9.0 + 2.0 / (9.0 * N), est["binder_se"]) < 4
 
 
 def test_high_temperature_series():
