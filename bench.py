@@ -119,11 +119,12 @@ BYTES_PER_ATTEMPT_FP32 = 24
 # launch of the workload's bench command, captured at full size (one ncu pass):
 # sc16 reads 0.75 MB (tables; the lattices stay in shared memory), large moves
 # 28.94 TB against 28.99 TB of algorithmic bytes, batched 328 GB (its streamed
-# L = 32 lattices, 402 GB algorithmic, partly served from L2).
+# L = 32 lattices, 402 GB algorithmic, partly served from L2), ising 0.50 MB.
 TRAFFIC = {
     "sc16": {"sources": "1353bf33dc85ee14", "bytes": 0.746e6},
     "large": {"sources": "1353bf33dc85ee14", "bytes": 14.44e12 + 14.50e12},
     "batched": {"sources": "1353bf33dc85ee14", "bytes": 129.70e9 + 198.21e9},
+    "ising": {"sources": "1353bf33dc85ee14", "bytes": 0.501e6},
 }
 
 
