@@ -208,7 +208,8 @@ def test_high_temperature_series():
 
 
 def test_low_temperature_equipartition():
-    """T -> 0 from the ordered start: e = -3J + T (1 - 1/N) + O(T^2).
+    """T -> 0 from the ordered start: e = -3J + T (1 - 1/N) + O(T^2), so the
+    heat capacity per spin C_V = N beta^2 (<e^2> - <e>^2) tends to 1 - 1/N.
 
     Two quadratic modes per spin, less the two of a global rotation, each carry
     T/2.  Acceptance is below 1% here, so thermalisation takes ~2000 sweeps.
@@ -222,6 +223,8 @@ def test_low_temperature_equipartition():
         ratio = (est["e"] + 3.0) / t
         # 4 SE plus an anharmonic allowance of 0.5 T
         assert abs(ratio - (1 - 1 / N)) < 4 * est["e_se"] / t + 0.5 * t
+        # the fluctuation estimator of Eq. (cv) gives the same limit
+        assert abs(est["cv"] - (1 - 1 / N)) < 4 * est["cv_se"] + t
 
 
 def test_ordered_start_frozen_at_zero_temperature():
