@@ -13,7 +13,8 @@ Readings (each listed in the design notes): a path's output is the mean over
 its measurement sweeps, so second moments are pooled means of per-path means
 of instantaneous squares; standard errors of derived quantities are
 delete-one jackknife over paths; the beta and h derivatives are the
-fluctuation formulas -N cov(O, e) and beta N cov(O, m_z).
+fluctuation formulas -N cov(O, e) and beta N cov(O, m_z), plus -<m_z> in
+d<e>/dh from the field term of e itself.
 """
 from __future__ import annotations
 
@@ -53,6 +54,56 @@ def _jackknife(stat, cols: dict[str, np.ndarray]) -> float:
     return float(np.sqrt((n - 1) / n * np.sum((th - th.mean()) ** 2)))
 
 
+# Derived quantities of Sec. 2.2 from pooled means m (record field -> mean over
+# paths), the sites per lattice N and beta = 1/T.  A Boltzmann average <A>
+# under the weight exp(-beta H), H = N e, moves with the parameters as
+#   d<A>/dbeta = <dA/dbeta> - cov(A, H) = -N cov(A, e)    (no A depends on beta),
+#   d<A>/dh    = <dA/dh> - beta cov(A, dH/dh) = <dA/dh> + beta N cov(A, m_z),
+# since dH/dh = -N m_z.  Of the observables only e = H/N depends on h itself
+# (de/dh = -m_z, its Zeeman part), so d<e>/dh carries the extra -<m_z>.
+def chi(m, N, beta):
+    """Eq. (cv), left: (N/T) (<|m|^2> - <|m|>^2)."""
+    return N * beta * (m["m2"] - m["m"] ** 2)
+
+
+def cv(m, N, beta):
+    """Eq. (cv), right: (N/T^2) (<e^2> - <e>^2)."""
+    return N * beta ** 2 * (m["e2"] - m["e"] ** 2)
+
+
+def binder(m, N, beta):
+    """Eq. (kum): 1 - <|m|^4> / (3 <|m|^2>^2)."""
+    return 1.0 - m["m4"] / (3.0 * m["m2"] ** 2)
+
+
+def de_dbeta(m, N, beta):
+    return -N * (m["e2"] - m["e"] ** 2)
+
+
+def dm_dbeta(m, N, beta):
+    return -N * (m["em"] - m["m"] * m["e"])
+
+
+def dmz_dbeta(m, N, beta):
+    return -N * (m["emz"] - m["mz"] * m["e"])
+
+
+def de_dh(m, N, beta):
+    return beta * N * (m["emz"] - m["e"] * m["mz"]) - m["mz"]
+
+
+def dm_dh(m, N, beta):
+    return beta * N * (m["mmz"] - m["m"] * m["mz"])
+
+
+def dmz_dh(m, N, beta):
+    return beta * N * (m["mz2"] - m["mz"] ** 2)
+
+
+DERIVED = dict(chi=chi, cv=cv, binder=binder, de_dbeta=de_dbeta, dm_dbeta=dm_dbeta,
+               dmz_dbeta=dmz_dbeta, de_dh=de_dh, dm_dh=dm_dh, dmz_dh=dmz_dh)
+
+
 def estimates(rec: np.ndarray, N: int, T: float) -> dict[str, float]:
     """Ensemble estimates of one system from its per-path records (paths x NREC)."""
     rec = np.asarray(rec, dtype=np.float64)
@@ -66,38 +117,9 @@ def estimates(rec: np.ndarray, N: int, T: float) -> dict[str, float]:
         out[k] = mean[k]
         out[k + "_se"] = se[k]
 
-    def chi(m):
-        return N * beta * (m["m2"] - m["m"] ** 2)
-
-    def cv(m):
-        return N * beta ** 2 * (m["e2"] - m["e"] ** 2)
-
-    def binder(m):
-        return 1.0 - m["m4"] / (3.0 * m["m2"] ** 2)
-
-    def de_dbeta(m):
-        return -N * (m["e2"] - m["e"] ** 2)
-
-    def dm_dbeta(m):
-        return -N * (m["em"] - m["m"] * m["e"])
-
-    def dmz_dbeta(m):
-        return -N * (m["emz"] - m["mz"] * m["e"])
-
-    def de_dh(m):
-        return beta * N * (m["emz"] - m["e"] * m["mz"])
-
-    def dm_dh(m):
-        return beta * N * (m["mmz"] - m["m"] * m["mz"])
-
-    def dmz_dh(m):
-        return beta * N * (m["mz2"] - m["mz"] ** 2)
-
-    derived = dict(chi=chi, cv=cv, binder=binder, de_dbeta=de_dbeta, dm_dbeta=dm_dbeta,
-                   dmz_dbeta=dmz_dbeta, de_dh=de_dh, dm_dh=dm_dh, dmz_dh=dmz_dh)
-    for name, f in derived.items():
-        out[name] = float(f(mean))
-        out[name + "_se"] = _jackknife(f, c)
+    for name, f in DERIVED.items():
+        out[name] = float(f(mean, N, beta))
+        out[name + "_se"] = _jackknife(lambda m, f=f: f(m, N, beta), c)
 
     # Eq. (eq:cv) for the order parameter <|M|>
     out["cv_m"] = se["m"] / mean["m"] if mean["m"] != 0 else float("nan")

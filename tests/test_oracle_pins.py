@@ -177,8 +177,12 @@ def test_free_spins_in_field():
     est = O.estimates(rec, 64, T)
     assert zdiff(est["mz"], langevin(x), est["mz_se"]) < 4
     assert zdiff(est["e"], -h * langevin(x), est["e_se"]) < 4
-    chi_z = (1.0 / x ** 2 - 1.0 / np.sinh(x) ** 2) / T
+    dL = 1.0 / x ** 2 - 1.0 / np.sinh(x) ** 2  # L'(x)
+    chi_z = dL / T
     assert zdiff(est["dmz_dh"], chi_z, est["dmz_dh_se"]) < 4
+    # <e> = -h L(beta h): d<e>/dh = -L(beta h) - beta h L'(beta h), the first term
+    # being the field term of e itself
+    assert zdiff(est["de_dh"], -langevin(x) - x * dL, est["de_dh_se"]) < 4
 
 
 def test_infinite_temperature():
@@ -332,3 +336,110 @@ def test_jackknife_of_mean_is_standard_error():
     x = np.random.default_rng(4).normal(size=333)
     se = x.std(ddof=1) / np.sqrt(x.size)
     assert _jackknife(lambda m: m["a"], {"a": x}) == pytest.approx(se, rel=1e-10)
+
+
+# --------------------------------------- derived estimators, two-spin chain --
+# Each fluctuation estimator of oracle/estimates.py is fed the exact averages of
+# the two-spin chain (tests/two_spin.py: 3-D quadrature, no sampling) and
+# compared with what fixes it independently: the central difference of the
+# exact <A>(beta, h) for the derivatives (d<e>/dT for C_V), and closed forms for
+# chi.  Then one Monte Carlo run of the oracle is compared with the same exact
+# values, and planted mistakes (a sign, a power of beta, a moment, a dropped
+# term) are shown to fail.
+import two_spin  # noqa: E402
+import importlib  # noqa: E402
+
+E = importlib.import_module("oracle.estimates")  # the module (the package re-exports a function of that name)
+
+TWO_SPIN_CASES = [(0.7, 1.0, 0.0), (0.7, 1.0, 0.3), (1.3, 1.0, -0.2), (0.5, -1.0, 0.4), (0.9, 0.0, 0.25)]
+DERIVATIVES = [("de_dbeta", "e", "beta"), ("dm_dbeta", "m", "beta"), ("dmz_dbeta", "mz", "beta"),
+               ("de_dh", "e", "h"), ("dm_dh", "m", "h"), ("dmz_dh", "mz", "h")]
+
+
+def _exact_estimates(beta, J, h):
+    rows = two_spin.record_rows(two_spin.moments(beta, J, h), O.REC, O.NREC)
+    return O.estimates(rows, 2, 1.0 / beta)
+
+
+def _central(obs, beta, J, h, param, step=1e-4):
+    if param == "beta":
+        p, q = two_spin.moments(beta + step, J, h), two_spin.moments(beta - step, J, h)
+    else:
+        p, q = two_spin.moments(beta, J, h + step), two_spin.moments(beta, J, h - step)
+    return (p[obs] - q[obs]) / (2 * step)
+
+
+def _check_two_spin_exact(beta, J, h):
+    est = _exact_estimates(beta, J, h)
+    for name, obs, param in DERIVATIVES:
+        fd = _central(obs, beta, J, h, param)
+        assert est[name] == pytest.approx(fd, rel=1e-6, abs=1e-8), (name, est[name], fd)
+    # C_V per site is d<e>/dT = -beta^2 d<e>/dbeta
+    fd_T = -beta ** 2 * _central("e", beta, J, h, "beta")
+    assert est["cv"] == pytest.approx(fd_T, rel=1e-6, abs=1e-8), ("cv", est["cv"], fd_T)
+    if h == 0.0 and J >= 0.0:
+        # chi of Eq. (cv) in closed form; the quadrature's <|m|> is good to ~1e-6
+        assert est["chi"] == pytest.approx(two_spin.chi_h0(beta, J), rel=2e-4), ("chi", est["chi"])
+
+
+@pytest.mark.parametrize("beta,J,h", TWO_SPIN_CASES + [(1.6, 0.0, 0.0), (0.35, 2.0, 0.0)])
+def test_derived_estimators_on_exact_two_spin_averages(beta, J, h):
+    _check_two_spin_exact(beta, J, h)
+
+
+def test_chi_closed_forms_of_two_spin_chain():
+    """The closed forms the chi pin uses: free pair chi = beta/9; at J > 0 the
+    erfi form of <|m|> agrees with direct quadrature of x ~ e^{Kx}."""
+    from scipy import integrate
+
+    assert two_spin.chi_h0(1.6, 0.0) == pytest.approx(1.6 / 9.0, rel=1e-15)
+    for K in (0.35, 0.7, 1.3, 3.0):
+        num, _ = integrate.quad(lambda x: np.sqrt((1 + x) / 2) * np.exp(K * x), -1, 1, epsabs=1e-14)
+        den = 2 * np.sinh(K) / K
+        assert two_spin.abs_m_h0(K) == pytest.approx(num / den, rel=1e-10)
+
+
+def test_derived_estimators_on_two_spin_monte_carlo():
+    """The oracle's sampled two-spin chain in a field against the exact values,
+    every estimate within 4 jackknife standard errors."""
+    beta, J, h = 0.7, 1.0, 0.3
+    rec = O.run([O.System(L=2, T=1.0 / beta, J=J, h=h, n_paths=4096, lattice=O.CHAIN)], 100, 400, seed=5)[0]
+    est = O.estimates(rec, 2, 1.0 / beta)
+    exact = _exact_estimates(beta, J, h)
+    for k in ("e", "m", "m2", "mz", "chi", "cv", "binder") + tuple(d[0] for d in DERIVATIVES):
+        assert zdiff(est[k], exact[k], est[k + "_se"]) < 4, (k, est[k], exact[k], est[k + "_se"])
+    # and at h = 0, J = 0.9: chi against its closed form
+    rec0 = O.run([O.System(L=2, T=1.0 / beta, J=0.9, n_paths=4096, lattice=O.CHAIN)], 100, 400, seed=6)[0]
+    est0 = O.estimates(rec0, 2, 1.0 / beta)
+    assert zdiff(est0["chi"], two_spin.chi_h0(beta, 0.9), est0["chi_se"]) < 4
+
+
+PLANTED = {
+    "chi": [lambda m, N, b: N * b ** 2 * (m["m2"] - m["m"] ** 2),       # T^2 for T
+            lambda m, N, b: N * b * (m["mz2"] - m["m"] ** 2),           # m_z^2 for |m|^2
+            lambda m, N, b: b * (m["m2"] - m["m"] ** 2)],               # N dropped
+    "cv": [lambda m, N, b: N * b * (m["e2"] - m["e"] ** 2)],            # T for T^2
+    "de_dbeta": [lambda m, N, b: N * (m["e2"] - m["e"] ** 2)],          # sign
+    "dm_dbeta": [lambda m, N, b: N * (m["em"] - m["m"] * m["e"]),       # sign
+                 lambda m, N, b: -N * (m["emz"] - m["m"] * m["e"])],    # e m_z for e |m|
+    "dmz_dbeta": [lambda m, N, b: N * (m["emz"] - m["mz"] * m["e"]),    # sign
+                  lambda m, N, b: -N * b * (m["emz"] - m["mz"] * m["e"])],  # stray beta
+    "de_dh": [lambda m, N, b: b * N * (m["emz"] - m["e"] * m["mz"]),    # explicit -<m_z> dropped
+              lambda m, N, b: b * N * (m["emz"] - m["e"] * m["mz"]) + m["mz"]],  # its sign
+    "dm_dh": [lambda m, N, b: N * (m["mmz"] - m["m"] * m["mz"]),        # beta dropped
+              lambda m, N, b: b * N * (m["em"] - m["m"] * m["e"])],     # e for m_z
+    "dmz_dh": [lambda m, N, b: b * N * (m["mz2"] - m["mz"] * m["m"])],  # |m| for m_z
+}
+
+
+@pytest.mark.parametrize("name,k", [(n, k) for n, fs in PLANTED.items() for k in range(len(fs))])
+def test_planted_estimator_mistakes_fail_the_pins(monkeypatch, name, k):
+    monkeypatch.setitem(E.DERIVED, name, PLANTED[name][k])
+    failed = False
+    for case in TWO_SPIN_CASES + [(1.6, 0.0, 0.0), (0.35, 2.0, 0.0)]:
+        try:
+            _check_two_spin_exact(*case)
+        except AssertionError:
+            failed = True
+            break
+    assert failed, f"planted mistake {name}[{k}] passed every pin"
