@@ -142,7 +142,8 @@ enum {
  *   cv       = (N/T^2) (<e^2> - <e>^2)                       Eq. (cv), right
  *   binder   = 1 - <|m|^4> / (3 <|m|^2>^2)                   Eq. (kum)
  *   dX_dbeta = -N (<X e> - <X><e>)       (fluctuation formula, X in {e,|m|,m_z})
- *   dX_dh    = beta N (<X m_z> - <X><m_z>)
+ *   dX_dh    = beta N (<X m_z> - <X><m_z>) + <dX/dh>, where only X = e has
+ *              an explicit field term: de/dh = -m_z, so de_dh carries -<m_z>
  *   cv_m     = se(<|m|>) / <|m|>                             Eq. (eq:cv)
  *   r_*      = 1 - ||R||^2 / ((P-1) sigma^2) of the normal Q-Q line fit of the
  *              per-path values, plotting positions (i - 1/2)/P,
@@ -271,7 +272,8 @@ int mp_spins(mp_handle h, int system, int64_t path, double* host_out, int64_t ca
  *   d_grad_beta[s] = g_e[s] d<e>/dbeta + g_m[s] d<|m|>/dbeta
  *   d_grad_h[s]    = g_e[s] d<e>/dh    + g_m[s] d<|m|>/dh
  * with d/dbeta = -N cov(., e), d/dh = beta N cov(., m_z) over the per-path
- * pooled moments (the estimators of C_V and chi, Eq. (cv)).  All four arrays
+ * pooled moments (the estimators of C_V and chi, Eq. (cv)), plus -<m_z> in
+ * d<e>/dh from the field term of e itself.  All four arrays
  * are device memory of n_systems doubles, owned by the caller; the kernel is
  * queued on the handle's stream after the last run.
  * Errors: MP_EINVAL (NULL pointer), MP_ESTATE (no run yet), MP_ECUDA. */

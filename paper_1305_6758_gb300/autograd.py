@@ -1,10 +1,13 @@
 """Differentiable ensemble observables: <e> and <|m|> as functions of (beta, h).
 
 The Boltzmann average of an observable O depends on beta and h through the
-weight exp(-beta H), H = -J sum S.S - h sum S^z, so (fluctuation-dissipation)
-  d<O>/dbeta = -N (<O e> - <O><e>),   d<O>/dh = beta N (<O m_z> - <O><m_z>),
-the estimators behind C_V and chi of Eq. (cv) in Sec. 2.2.  The forward pass
-is a multipath run (one system per (beta, h) pair); the backward pass is the
+weight exp(-beta H), H = -J sum S.S - h sum S^z = N e, so (fluctuation-dissipation)
+  d<O>/dbeta = -N (<O e> - <O><e>),
+  d<O>/dh    = beta N (<O m_z> - <O><m_z>) + <dO/dh>,
+the estimators behind C_V and chi of Eq. (cv) in Sec. 2.2.  Only O = e has
+an explicit field term (de/dh = -m_z), so
+  d<e>/dh = beta N (<e m_z> - <e><m_z>) - <m_z>,   d<|m|>/dh = beta N cov(|m|, m_z).
+The forward pass is a multipath run (one system per (beta, h) pair); the backward pass is the
 library's covariance kernel over the per-path pooled moments, weighted by the
 upstream gradients.
 

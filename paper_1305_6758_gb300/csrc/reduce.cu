@@ -59,7 +59,10 @@ __device__ double block_max(double v, double* scratch) {
 }
 
 // chi, C_V, U_L and the six fluctuation derivatives from pooled means
-// (indexed by MP_R_*).
+// (indexed by MP_R_*).  Under the weight exp(-beta N e):
+//   d<A>/dbeta = -N cov(A, e),   d<A>/dh = <dA/dh> + beta N cov(A, m_z),
+// and of A in {e, |m|, m_z} only e = (-J E_bonds - h M_z)/N depends on h
+// itself (de/dh = -m_z).
 __device__ void derived(const double* mu, double N, double beta, double* th) {
   const double e = mu[MP_R_E], e2 = mu[MP_R_E2], m = mu[MP_R_M], m2 = mu[MP_R_M2];
   const double m4 = mu[MP_R_M4], mz = mu[MP_R_MZ], mz2 = mu[MP_R_MZ2];
@@ -70,7 +73,7 @@ __device__ void derived(const double* mu, double N, double beta, double* th) {
   th[3] = -N * (e2 - e * e);                // d<e>/dbeta
   th[4] = -N * (em - m * e);                // d<|m|>/dbeta
   th[5] = -N * (emz - mz * e);              // d<m_z>/dbeta
-  th[6] = beta * N * (emz - e * mz);        // d<e>/dh
+  th[6] = beta * N * (emz - e * mz) - mz;   // d<e>/dh: e's own field term adds -<m_z>
   th[7] = beta * N * (mmz - m * mz);        // d<|m|>/dh
   th[8] = beta * N * (mz2 - mz * mz);       // d<m_z>/dh
 }
@@ -293,8 +296,9 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const ReduceParams 
 
 // Covariance backward: for each system, with upstream gradients (g_e, g_m) of
 // (<e>, <|m|>),  dL/dbeta = -N [g_e cov(e, e) + g_m cov(|m|, e)]  and
-// dL/dh = beta N [g_e cov(e, m_z) + g_m cov(|m|, m_z)], covariances of the
-// pooled per-path moments (the C_V / chi estimators of Eq. (cv)).
+// dL/dh = beta N [g_e cov(e, m_z) + g_m cov(|m|, m_z)] - g_e <m_z> (the last
+// term from the field part of e), covariances of the pooled per-path moments
+// (the C_V / chi estimators of Eq. (cv)).
 __global__ void __launch_bounds__(kRedThreads) backward_kernel(const BackwardParams p) {
   __shared__ double scratch[32 * 8];
   const int sidx = blockIdx.x;
@@ -320,7 +324,7 @@ __global__ void __launch_bounds__(kRedThreads) backward_kernel(const BackwardPar
     const double N = static_cast<double>(sy.N), beta = sy.beta;
     const double ge = p.g_e[sidx], gm = p.g_m[sidx];
     p.grad_beta[sidx] = -N * (ge * (e2 - e * e) + gm * (em - m * e));
-    p.grad_h[sidx] = beta * N * (ge * (emz - e * mz) + gm * (mmz - m * mz));
+    p.grad_h[sidx] = beta * N * (ge * (emz - e * mz) + gm * (mmz - m * mz)) - ge * mz;
   }
 }
 

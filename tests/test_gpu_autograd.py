@@ -75,3 +75,29 @@ def test_l16_gradients_against_central_differences(h0):
         se_fd = np.sqrt(p["e_se"] ** 2 + q["e_se"] ** 2 + p["m_se"] ** 2 + q["m_se"] ** 2) / (2 * step)
         se_grad = np.hypot(se_e, se_m)
         assert abs(grad - fd) < 4 * np.hypot(se_fd, se_grad), (name, grad, fd, se_fd, se_grad)
+
+
+def test_l16_energy_field_derivative_against_central_difference():
+    """d<e>/dh alone at h = 0.01 in the ordered phase (beta = 0.8, L = 16): the
+    field aligns the magnetisation, so the -<m_z> term of d<e>/dh dominates.
+    Autograd against the central difference of <e> (step 1e-3) of independent
+    runs within 4 combined SE, and the formula without that term fails."""
+    spec = dict(L=16, n_paths=4096, n_therm=1000, n_meas=1000)
+    beta, h0, step = 0.8, 0.01, 1e-3
+    e, m, b, f = _grads([beta], [h0], seed=1, **spec)
+    e.sum().backward()
+    with mp.Simulation([mp.System(16, 1 / beta, h=h0, n_paths=4096)], 1000, 1000, seed=1) as sim:
+        sim.run()
+        est = sim.estimates(0)
+    assert f.grad.item() == pytest.approx(est["de_dh"], rel=1e-12)
+    runs = []
+    for k, dh in enumerate((step, -step)):
+        with mp.Simulation([mp.System(16, 1 / beta, h=h0 + dh, n_paths=4096)], 1000, 1000,
+                           seed=200 + k) as sim:
+            sim.run()
+            runs.append(sim.estimates(0))
+    fd = (runs[0]["e"] - runs[1]["e"]) / (2 * step)
+    se = np.hypot(np.hypot(runs[0]["e_se"], runs[1]["e_se"]) / (2 * step), est["de_dh_se"])
+    assert abs(f.grad.item() - fd) < 4 * se, (f.grad.item(), fd, se)
+    print("d<e>/dh", f.grad.item(), "central difference", fd, "SE", se, "<m_z>", est["mz"])
+    assert abs(f.grad.item() + est["mz"] - fd) > 4 * se

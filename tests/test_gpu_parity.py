@@ -188,6 +188,33 @@ def test_open_chain_closed_form_and_backward():
     assert gh2.item() == pytest.approx(est["dm_dh"], rel=1e-9, abs=1e-12)
 
 
+def test_field_derivatives_reduction_and_backward():
+    """h != 0: the reduction's field and temperature derivatives (d<e>/dh with
+    the -<m_z> of e's own field term) equal the oracle's estimates of the same
+    records, the backward kernel equals them, and for free spins (J = 0)
+    d<e>/dh = -L(beta h) - beta h L'(beta h) within 4 SE."""
+    systems = [mp.System(4, 1.0, h=0.3, n_paths=512), mp.System(4, 0.5, J=0.0, h=0.3, n_paths=512)]
+    with mp.Simulation(systems, 100, 400, seed=9, precision=mp.FP64) as sim:
+        sim.run()
+        recs = [sim.paths(k) for k in range(2)]
+        ests = [sim.estimates(k) for k in range(2)]
+        gb, gh = sim.backward([1.0, 1.0], [0.0, 0.0])
+        gb2, gh2 = sim.backward([0.0, 0.0], [1.0, 1.0])
+    for k, s in enumerate(systems):
+        oest = O.estimates(recs[k], 64, s.T)
+        for key in ("chi", "cv", "binder", "de_dbeta", "dm_dbeta", "dmz_dbeta", "de_dh", "dm_dh", "dmz_dh"):
+            assert ests[k][key] == pytest.approx(oest[key], rel=1e-9, abs=1e-12), key
+            assert ests[k][key + "_se"] == pytest.approx(oest[key + "_se"], rel=1e-7, abs=1e-12), key
+        assert gb[k].item() == pytest.approx(ests[k]["de_dbeta"], rel=1e-9)
+        assert gh[k].item() == pytest.approx(ests[k]["de_dh"], rel=1e-9)
+        assert gb2[k].item() == pytest.approx(ests[k]["dm_dbeta"], rel=1e-9)
+        assert gh2[k].item() == pytest.approx(ests[k]["dm_dh"], rel=1e-9)
+    x = 0.3 / 0.5
+    lang = 1 / np.tanh(x) - 1 / x
+    closed = -lang - x * (1 / x**2 - 1 / np.sinh(x) ** 2)
+    assert abs(ests[1]["de_dh"] - closed) < 4 * ests[1]["de_dh_se"], (ests[1]["de_dh"], closed)
+
+
 # ---------------------------------------------------------------- errors ---
 def test_status_codes():
     with pytest.raises(mp.MPError) as ei:
