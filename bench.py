@@ -67,7 +67,7 @@ WORKLOADS = {
               "FP64 reductions")),
     "plain": dict(
         systems=[(4, 1.5, 256)], n_therm=1000, n_meas=1000, precision="fp64", bound="alu",
-        cpu_paths=256, ref_paths=256, fp64_paths=0,
+        cpu_paths=256, ref_paths=16, fp64_paths=0,
         text=("plain method, FP64: simple cubic L=4, J=1, h=0, T=1.5, 256 paths, 1000+1000 "
               "checkerboard sweeps")),
     "ising": dict(
@@ -159,13 +159,22 @@ def attempts_of(systems, sweeps, paths_override=None):
     return sum(sites(e) * (paths_override or e[2]) * sweeps for e in systems)
 
 
-def oracle_sample(w, paths_per_system: int, threads: int | None = None):
-    """Run the FP64 oracle on the first paths of every system; returns (attempts, seconds)."""
+def oracle_sample(w, paths_per_system: int, threads: int | None = None, total_paths: int | None = None):
+    """Run the FP64 oracle on the first paths of every system; returns (attempts, seconds).
+
+    With total_paths, that many paths are dealt round-robin over the systems
+    (path j of the sample is path j // n_systems of system j % n_systems), so
+    that a sample of exactly `threads` equal paths keeps every host core busy.
+    """
     import oracle
 
     oracle.build()
-    systems = [oracle.System(e[0], e[1], n_paths=e[2], path_begin=0, path_count=min(paths_per_system, e[2]),
-                             lattice=lattice_of(e)) for e in w["systems"]]
+    ns = len(w["systems"])
+    counts = ([min(paths_per_system, e[2]) for e in w["systems"]] if total_paths is None else
+              [min(e[2], total_paths // ns + (1 if k < total_paths % ns else 0))
+               for k, e in enumerate(w["systems"])])
+    systems = [oracle.System(e[0], e[1], n_paths=e[2], path_begin=0, path_count=c, lattice=lattice_of(e))
+               for e, c in zip(w["systems"], counts) if c > 0]
     order = oracle.ORDER_RANDOM if w.get("order") == "random" else oracle.ORDER_CHECKER
     t0 = time.perf_counter()
     oracle.run(systems, w["n_therm"], w["n_meas"], seed=1, threads=threads, order_mode=order)
@@ -244,16 +253,19 @@ def run_reference(args, w, rank):
     if rank != 0:
         return
     cores = os.cpu_count() or 1
+    # one path per host core per step, dealt round-robin over the systems
+    n_ref = min(cores * w["ref_paths"], sum(e[2] for e in w["systems"]))
     for _ in range(args.warmup):
-        oracle_sample(w, w["ref_paths"], cores)
+        oracle_sample(w, 0, cores, total_paths=n_ref)
     total_att, total_s = 0, 0.0
     for _ in range(args.steps):
-        att, dt = oracle_sample(w, w["ref_paths"], cores)
+        att, dt = oracle_sample(w, 0, cores, total_paths=n_ref)
         total_att += att
         total_s += dt
     value = total_att / total_s
-    sample = (f"{w['ref_paths']} path(s) of each of the {len(w['systems'])} systems, all "
-              f"{w['n_therm'] + w['n_meas']} sweeps, per step (FP64 oracle, {cores} threads)")
+    sample = (f"{n_ref} paths per step (up to {w['ref_paths']} per host core), dealt round-robin over the "
+              f"{len(w['systems'])} systems, all {w['n_therm'] + w['n_meas']} sweeps (FP64 oracle, "
+              f"{cores} threads)")
     emit({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "attempts/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -266,6 +278,138 @@ def run_reference(args, w, rank):
     })
 
 
+def make_systems(mp, w, paths_override=None):
+    return [mp.System(e[0], e[1], n_paths=paths_override or e[2], lattice=lattice_of(e)) for e in w["systems"]]
+
+
+def timed_runs(mp, torch, w, dev, seed, steps, warmup, flush, barrier, gpu_id, nvtx=None):
+    """W untimed runs, then K runs each bracketed by CUDA events on the
+    simulation's own stream (L2 flushed before each); the clocks are sampled
+    during the timed runs.  Returns the simulation (open) and the timings."""
+    precision = mp.FP64 if w["precision"] == "fp64" else mp.FP32
+    tune = mp.FLAG_AUTOTUNE | (mp.FLAG_RANDOM_SITE if w.get("flags") == "random_site" else 0)
+    sim = mp.Simulation(make_systems(mp, w), w["n_therm"], w["n_meas"], seed=seed, precision=precision,
+                        device=dev, flags=tune)
+    for _ in range(warmup):
+        sim.run()
+    barrier()
+    clocks = ClockSampler(gpu_id)
+    step_ms, sweep_ms, reduce_ms = [], [], []
+    barrier()
+    if nvtx:
+        # an NVTX range around the timed steps lets a profiler select their launches
+        torch.cuda.nvtx.range_push(nvtx)
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(sim.stream)
+        sim.run()
+        e1.record(sim.stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        a, b = sim.timing()
+        sweep_ms.append(a)
+        reduce_ms.append(b)
+    if nvtx:
+        torch.cuda.nvtx.range_pop()
+    barrier()
+    return sim, dict(step_ms=step_ms, sweep_ms=sweep_ms, reduce_ms=reduce_ms, clocks=clocks.stop(),
+                     precision=precision, tune=tune)
+
+
+def roofline_of(name, w, sweep_avg_ms, n_sm, full_size):
+    """The dominant kernel against its roofline: ALU issue for lattices held in
+    shared memory, HBM bandwidth for streamed ones (algorithmic units per launch
+    / the kernel's average event-timed duration)."""
+    peaks, peak_kind = load_peaks()
+    kernel_rate = attempts_of(w["systems"], w["n_therm"] + w["n_meas"]) / (sweep_avg_ms / 1e3)
+    if w["bound"] == "hbm":
+        peak = float(peaks["hbm_gbs"])
+        achieved = BYTES_PER_ATTEMPT_FP32 * kernel_rate / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": launch_traffic(name) if full_size else None,
+                "bytes_per_attempt": BYTES_PER_ATTEMPT_FP32,
+                "peak_basis": f"{peak_kind} HBM copy bandwidth"}
+    else:
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = n_sm * 128 * sm_max * 1e6 / 1e12  # lane-ops/s in units of 1e12
+        ops = OPS_PER_ATTEMPT_ISING if w["bound"] == "alu_ising" else OPS_PER_ATTEMPT
+        achieved = ops * kernel_rate / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                "traffic": launch_traffic(name) if full_size else None, "ops_per_attempt": ops,
+                "peak_basis": f"{n_sm} SMs x 128 lanes x {sm_max:.0f} MHz ({peak_kind} max clock)"}
+    kernel = {"ising": "ising_kernel", "random_site": "random_site_kernel"}.get(
+        "ising" if w["bound"] == "alu_ising" else w.get("flags"), "sweep_kernel")
+    roof.update(kernel=kernel, sweep_ms=sweep_avg_ms)
+    return roof, kernel_rate
+
+
+# Estimates of Sec. 2.2 from pooled per-path means (record columns), for the
+# paired FP32 - FP64 comparison below: chi and C_V of Eq. (cv), U_L of Eq. (kum).
+REC_COL = {"e": 0, "e2": 1, "m": 2, "m2": 3, "m4": 4}
+
+
+def _estimate(key, mu, N, beta):
+    e, e2, m, m2, m4 = (mu[..., REC_COL[k]] for k in ("e", "e2", "m", "m2", "m4"))
+    if key == "chi":
+        return N * beta * (m2 - m * m)
+    if key == "cv":
+        return N * beta * beta * (e2 - e * e)
+    if key == "binder":
+        return 1.0 - m4 / (3.0 * m2 * m2)
+    return mu[..., REC_COL[key]]
+
+
+def paired_difference(rec_a, rec_b, key, N, beta):
+    """Estimate of run a minus that of run b over the same paths, and its
+    delete-one jackknife standard error (one path left out of both runs)."""
+    import numpy as np
+
+    P = rec_a.shape[0]
+    d = float(_estimate(key, rec_a.mean(axis=0), N, beta) - _estimate(key, rec_b.mean(axis=0), N, beta))
+    la = (rec_a.sum(axis=0) - rec_a) / (P - 1)
+    lb = (rec_b.sum(axis=0) - rec_b) / (P - 1)
+    th = _estimate(key, la, N, beta) - _estimate(key, lb, N, beta)
+    return d, float(np.sqrt((P - 1) / P * np.sum((th - th.mean()) ** 2)))
+
+
+def precision_record(mp, torch, w, dev, seed):
+    """FP32 against the FP64 GPU form on the same paths and seed (paired), at
+    three temperatures of the scan; also the FP64 form's throughput."""
+    temps, P = (0.5, 1.5, 2.5), 1024
+    L = w["systems"][0][0]
+    N = L ** 3
+    systems = [mp.System(L, T, n_paths=P) for T in temps]
+    out = {}
+    for prec in (mp.FP32, mp.FP64):
+        with mp.Simulation(systems, w["n_therm"], w["n_meas"], seed=seed, precision=prec, device=dev) as sim:
+            sim.run()
+            torch.cuda.synchronize(dev)
+            sweep_ms, _ = sim.timing()
+            out[prec] = ([sim.paths(k) for k in range(len(temps))], [sim.estimates(k) for k in range(len(temps))],
+                         sweep_ms)
+    rows = []
+    for k, T in enumerate(temps):
+        r32, e32 = out[mp.FP32][0][k], out[mp.FP32][1][k]
+        r64, e64 = out[mp.FP64][0][k], out[mp.FP64][1][k]
+        row = {"T": T}
+        for key, se_key in (("e", "e_se"), ("m", "m_se"), ("chi", "chi_se"), ("cv", "cv_se"),
+                            ("binder", "binder_se")):
+            d, pse = paired_difference(r32, r64, key, N, 1.0 / T)
+            row[key] = {"fp32": e32[key], "fp64": e64[key], "diff": d, "paired_se": pse,
+                        "combined_se": (e32[se_key] ** 2 + e64[se_key] ** 2) ** 0.5}
+        rows.append(row)
+    att64 = N * P * len(temps) * (w["n_therm"] + w["n_meas"])
+    v64 = att64 / (out[mp.FP64][2] / 1e3)
+    return rows, {"value": v64, "unit": "attempts/s",
+                  "sample": f"L={L}, T in {list(temps)}, {P} paths each, {w['n_therm']}+{w['n_meas']} sweeps"}
+
+
+# Sub-workloads timed beside the headline (default) workload: (steps, warmup).
+SUBRECORDS = {"batched": (5, 2), "large": (2, 1)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -275,6 +419,7 @@ def main():
     ap.add_argument("--workload", default="sc16", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-sub", action="store_true", help="skip the batched and large sub-records")
     # shorter runs of the same launch (for profiling captures only)
     ap.add_argument("--n-therm", type=int, default=None)
     ap.add_argument("--n-meas", type=int, default=None)
@@ -319,49 +464,26 @@ def main():
     seed = 1 + rank
     n_therm, n_meas = w["n_therm"], w["n_meas"]
     sweeps = n_therm + n_meas
-    precision = mp.FP64 if w["precision"] == "fp64" else mp.FP32
-    systems = [mp.System(e[0], e[1], n_paths=e[2], lattice=lattice_of(e)) for e in w["systems"]]
-    n_sys = len(systems)
-    tune = mp.FLAG_AUTOTUNE | (mp.FLAG_RANDOM_SITE if w.get("flags") == "random_site" else 0)
-    sim = mp.Simulation(systems, n_therm, n_meas, seed=seed, precision=precision, device=dev, flags=tune)
-    stream = sim.stream
+    n_sys = len(w["systems"])
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
-
-    for _ in range(args.warmup):
-        sim.run()
-    barrier()
-
     props = torch.cuda.get_device_properties(dev)
     gpu_id = str(getattr(props, "uuid", local_rank))
     if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) == 36:
         gpu_id = "GPU-" + gpu_id
-    clocks = ClockSampler(gpu_id)
-    step_ms, sweep_ms, reduce_ms = [], [], []
-    barrier()
-    # an NVTX range around the timed steps lets a profiler select their launches
-    torch.cuda.nvtx.range_push("timed")
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        sim.run()
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        a, b = sim.timing()
-        sweep_ms.append(a)
-        reduce_ms.append(b)
-    torch.cuda.nvtx.range_pop()
-    barrier()
-    clk = clocks.stop()
+    n_sm = props.multi_processor_count
 
-    total_ms = max_over_ranks(sum(step_ms), dist, dev)
+    sim, t = timed_runs(mp, torch, w, dev, seed, args.steps, args.warmup, flush, barrier, gpu_id, nvtx="timed")
+    precision, tune = t["precision"], t["tune"]
+    systems = make_systems(mp, w)
+    total_ms = max_over_ranks(sum(t["step_ms"]), dist, dev)
     attempts_rank = attempts_of(w["systems"], sweeps)
     paths_rank = sum(e[2] for e in w["systems"])
     value = job_throughput(attempts_rank, world, args.steps, total_ms)
     paths_per_s = job_throughput(paths_rank, world, args.steps, total_ms)
     ests = [sim.estimates(k) for k in range(n_sys)]
+    plan_main = sim.plan()
+    autotuned = [sim.system_plan(k) for k in (range(n_sys) if n_sys <= 8 else sorted({0, n_sys // 2, n_sys - 1}))]
+    sim.close()
 
     # end to end through the public API: create (system and work tables H2D),
     # run, read every system's estimates (D2H), destroy -- all inside the clock;
@@ -384,44 +506,33 @@ def main():
     d2h_total = ctypes.sizeof(mp.MPEstimates) * n_sys
     e2e_value = attempts_rank * world / (sum(e2e_s) / len(e2e_s))
 
-    peaks, peak_kind = load_peaks()
-    sweep_avg = sum(sweep_ms) / len(sweep_ms)
-    kernel_rate = attempts_rank / (sweep_avg / 1e3)
-    n_sm = props.multi_processor_count
-    if w["bound"] == "hbm":
-        peak = float(peaks["hbm_gbs"])
-        achieved = BYTES_PER_ATTEMPT_FP32 * kernel_rate / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": launch_traffic(args.workload) if full_size else None,
-                "bytes_per_attempt": BYTES_PER_ATTEMPT_FP32,
-                "peak_basis": f"{peak_kind} HBM copy bandwidth"}
-    else:
-        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-        peak = n_sm * 128 * sm_max * 1e6 / 1e12  # lane-ops/s in units of 1e12
-        ops = OPS_PER_ATTEMPT_ISING if w["bound"] == "alu_ising" else OPS_PER_ATTEMPT
-        achieved = ops * kernel_rate / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": launch_traffic(args.workload) if full_size else None, "ops_per_attempt": ops,
-                "peak_basis": f"{n_sm} SMs x 128 lanes x {sm_max:.0f} MHz ({peak_kind} max clock)"}
-    kernel = {"ising": "ising_kernel", "random_site": "random_site_kernel"}.get(
-        "ising" if w["bound"] == "alu_ising" else w.get("flags"), "sweep_kernel")
-    roof.update(kernel=kernel, sweep_ms=sweep_avg, reduce_ms=sum(reduce_ms) / len(reduce_ms))
+    sweep_avg = sum(t["sweep_ms"]) / len(t["sweep_ms"])
+    roof, kernel_rate = roofline_of(args.workload, w, sweep_avg, n_sm, full_size)
+    roof["reduce_ms"] = sum(t["reduce_ms"]) / len(t["reduce_ms"])
 
-    fp64 = None
-    if w["fp64_paths"] and not args.no_fp64 and precision == mp.FP32:
-        sub = w["fp64_paths"]
-        with mp.Simulation([mp.System(e[0], e[1], n_paths=sub, lattice=lattice_of(e)) for e in w["systems"]],
-                           n_therm, n_meas,
-                           seed=seed, precision=mp.FP64, device=dev) as s64:
-            s64.run()
-            torch.cuda.synchronize(dev)
-            a64, _ = s64.timing()
-            e64 = [s64.estimates(k) for k in range(n_sys)]
-        v64 = attempts_of(w["systems"], sweeps, sub) / (a64 / 1e3)
-        worst = max(abs(ests[k]["e"] - e64[k]["e"]) / (ests[k]["e_se"] ** 2 + e64[k]["e_se"] ** 2) ** 0.5
-                    for k in range(n_sys))
-        fp64 = {"value": v64, "unit": "attempts/s", "sample": f"{sub} paths per system, same sweeps",
-                "fp32_over_fp64": kernel_rate / v64, "max_e_diff_in_combined_se": worst}
+    # FP32 against the FP64 GPU form, estimate by estimate (paired over the
+    # same paths), and the FP64 form's throughput on the same lattice
+    fp64, prec_rows = None, None
+    if w["fp64_paths"] and not args.no_fp64 and precision == mp.FP32 and full_size:
+        prec_rows, fp64 = precision_record(mp, torch, w, dev, seed)
+        fp64["fp32_over_fp64"] = kernel_rate / fp64["value"]
+
+    # the batch of uneven sizes (the target form) and the large streamed
+    # lattice, each timed on its own beside the headline workload
+    subs = {}
+    if args.workload == "sc16" and full_size and not args.no_sub:
+        for name, (k_steps, k_warm) in SUBRECORDS.items():
+            ws = WORKLOADS[name]
+            s_sim, st = timed_runs(mp, torch, ws, dev, seed, k_steps, k_warm, flush, barrier, gpu_id)
+            s_plan = s_sim.plan()
+            s_sim.close()
+            s_ms = max_over_ranks(sum(st["step_ms"]), dist, dev)
+            s_att = attempts_of(ws["systems"], ws["n_therm"] + ws["n_meas"])
+            s_roof, _ = roofline_of(name, ws, sum(st["sweep_ms"]) / len(st["sweep_ms"]), n_sm, True)
+            subs[name] = {"value": job_throughput(s_att, world, k_steps, s_ms), "unit": "attempts/s",
+                          "steps": k_steps, "warmup": k_warm, "ms_per_step": s_ms / k_steps,
+                          "config": {"workload": ws["text"], "plan": s_plan}, "roofline": s_roof,
+                          "clocks": st["clocks"], "gpu_launches": 2 * k_steps}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -432,20 +543,20 @@ def main():
                          f"({att:.3g} attempts, {dt:.1f} s)"}
 
     if rank == 0:
-        emit({
+        line = {
             "metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if precision == mp.FP64 else "f32", "data": "synthetic",
             "config": {"workload": w["text"], "name": args.workload, "n_therm": n_therm, "n_meas": n_meas,
-                       "systems": len(systems), "paths": paths_rank, "parallelism": f"replicas x{world}",
-                       "l2": "flushed between timed steps (256 MB write)", "plan": sim.plan(),
-                       "autotuned": [sim.system_plan(k) for k in
-                                     (range(n_sys) if n_sys <= 8 else sorted({0, n_sys // 2, n_sys - 1}))]},
+                       "systems": n_sys, "paths": paths_rank, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between timed steps (256 MB write)", "plan": plan_main,
+                       "autotuned": autotuned},
             "paths_per_s": paths_per_s,
             "sigma": {"e_se_max": max(e["e_se"] for e in ests), "m_se_max": max(e["m_se"] for e in ests),
                       "e": [[e["T"], e["e"], e["e_se"]] for e in ests[:: max(1, n_sys // 3)]]},
             "fp64_form": fp64,
+            "precision": prec_rows,
             "e2e": {"value": e2e_value, "unit": "attempts/s", "h2d_bytes_per_step": h2d_total,
                     "d2h_bytes_per_step": d2h_total,
                     "layout": ("autotuned once per process: each step's new handle takes the layout "
@@ -453,9 +564,11 @@ def main():
             "gpu_launches": 2 * args.steps,
             "roofline": roof,
             "cpu_baseline": cpu,
-            "clocks": clk,
-        })
-    sim.close()
+            "clocks": t["clocks"],
+        }
+        if subs:
+            line["workloads"] = subs
+        emit(line)
     if dist is not None:
         dist.destroy_process_group()
 
