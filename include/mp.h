@@ -330,9 +330,12 @@ int mp_restore(mp_handle h, const void* buf, size_t nbytes);
  * run is in flight. */
 int mp_cancel(mp_handle h);
 
-/* Launch shape of one system: threads per path, paths per CTA, and whether
- * its lattice is streamed from HBM (1) or held in shared memory (0).  Any
- * output may be NULL.  Errors: MP_EINVAL (bad index). */
+/* Launch shape of one system: threads per path, paths per CTA, and where
+ * its lattice lives during a run: 0 in one CTA's shared memory, 1 streamed
+ * from HBM, 2 split over the shared memory of the two CTAs of a cluster
+ * (FP32 simple cubic L = 32: each CTA holds half of the z-planes, one path
+ * per cluster, threads_per_path then counts one CTA).  Any output may be
+ * NULL.  Errors: MP_EINVAL (bad index). */
 int mp_system_plan(mp_handle h, int system, int* threads_per_path, int* paths_per_cta,
                    int* streamed_from_hbm);
 

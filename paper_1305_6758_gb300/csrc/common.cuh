@@ -45,6 +45,14 @@ struct DevSystem {
 
 constexpr int kModeShared = 0;
 constexpr int kModeStreamed = 1;
+constexpr int kModePair = 2;  // held in the shared memory of the two CTAs of a cluster
+// The lattice size held by two-CTA clusters (FP32 simple cubic L = 32: 393 KB
+// of spins), and the shared-memory bytes of one CTA's half with its two halo
+// planes per colour: 2 colours x (L/2 + 2) planes x L^2/2 sites x 3 values.
+constexpr int kPairL = 32;
+__host__ __device__ constexpr int pair_spin_bytes(int L, int real) {
+  return 2 * (L / 2 + 2) * (L * L / 2) * 3 * real;
+}
 
 // A unit of the persistent work queue: `count` consecutive paths of one
 // system, run side by side by one CTA (one thread group per path).
@@ -79,10 +87,17 @@ struct SweepParams {
   int32_t resume, save;
   const volatile int* cancel;   // host-mapped cancel flag, or nullptr
   const unsigned long long* ising_thr;  // Ising: 10 acceptance thresholds per system
+  // Paths held by the two CTAs of a cluster (kModePair): their work items
+  // (one path each) and queue counter.  n_pair_items > 0 requires a launch
+  // in clusters of two CTAs.
+  const WorkItem* pair_items;
+  int32_t n_pair_items;
+  int* pair_queue;
 };
 
 constexpr int kErrTimeout = 1;
 constexpr int kErrCanceled = 2;
+constexpr int kErrLaunch = 3;  // paths for two-CTA clusters in a launch without clusters
 constexpr int kStateHeader = 256;  // bytes before a path's spins in its state: acc[24], accepted
 constexpr int kCancelPoll = 16;    // sweeps between polls of the cancel flag
 

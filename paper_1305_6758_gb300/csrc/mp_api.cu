@@ -32,6 +32,8 @@ cudaError_t launch_sweep_fp32(int variant, const SweepParams& p, int grid, int c
                               cudaStream_t st);
 cudaError_t launch_sweep_fp64(int variant, const SweepParams& p, int grid, int cta, int smem,
                               cudaStream_t st);
+cudaError_t sweep_cluster_occupancy_fp32(int variant, int cta, int smem, int* clusters);
+cudaError_t sweep_cluster_occupancy_fp64(int variant, int cta, int smem, int* clusters);
 
 bool sweep_supports_L(int precision, int L) {
   return precision == MP_FP64 ? sweep_supports_L_fp64(L) : sweep_supports_L_fp32(L);
@@ -46,6 +48,10 @@ cudaError_t sweep_occupancy(int precision, int variant, int cta, int smem, int* 
   if (variant == kIsingKernel) return ising_occupancy(cta, smem, blocks);
   return precision == MP_FP64 ? sweep_occupancy_fp64(variant, cta, smem, blocks)
                               : sweep_occupancy_fp32(variant, cta, smem, blocks);
+}
+cudaError_t sweep_cluster_occupancy(int precision, int variant, int cta, int smem, int* clusters) {
+  return precision == MP_FP64 ? sweep_cluster_occupancy_fp64(variant, cta, smem, clusters)
+                              : sweep_cluster_occupancy_fp32(variant, cta, smem, clusters);
 }
 cudaError_t launch_sweep(int precision, int variant, const SweepParams& p, int grid, int cta,
                          int smem, cudaStream_t st) {
@@ -101,9 +107,17 @@ int round_up(int v, int m) { return (v + m - 1) / m * m; }
 // padded to 16 bytes, in bytes.
 int half_plane_bytes(int L, int real) { return round_up(3 * (L * L / 2) * real, 16); }
 
+// Lattices held in the shared memory of the two CTAs of a cluster: the FP32
+// simple cubic L = 32 (393 KB of spins, too large for one SM, not for two),
+// unless every lattice is to stream from HBM.
+bool paired(const mp_system& s, int precision, uint32_t flags) {
+  return s.lattice == MP_LATTICE_SC && s.L == kPairL && precision == MP_FP32 &&
+         !(flags & (MP_FLAG_STREAM | MP_FLAG_RANDOM_SITE));
+}
+
 bool streamed(const mp_system& s, int precision, uint32_t flags) {
   // the plane wavefront needs at least four planes
-  return s.lattice == MP_LATTICE_SC && s.L >= 4 &&
+  return s.lattice == MP_LATTICE_SC && s.L >= 4 && !paired(s, precision, flags) &&
          ((flags & MP_FLAG_STREAM) || !sweep_supports_L(precision, s.L));
 }
 
@@ -125,6 +139,7 @@ struct mp_state {
   std::vector<mp_system> systems;
   std::vector<DevSystem> hsys;
   std::vector<WorkItem> items;
+  std::vector<WorkItem> pair_items;  // one path each, for two-CTA clusters (after items in d_items)
   std::vector<int64_t> spin_offset;
   int64_t total_paths = 0, max_paths = 0, total_spins = 0;
 
@@ -297,9 +312,11 @@ int plan(mp_state* h, const mp_config* cfg) {
   h->max_paths = 0;
   // one kernel per lattice size when the batch has a single size; lattices
   // too large for shared memory are streamed from HBM (any size, one kernel)
+  // lattices held by two-CTA clusters run in the mixed-size kernel
   auto variant_of = [&](const mp_system& sy) {
     if (sy.lattice == MP_LATTICE_ISING) return kIsingKernel;
     if (sy.lattice == MP_LATTICE_CHAIN) return -1;
+    if (paired(sy, h->precision, h->flags)) return 0;  // the mixed-size kernel
     if (!streamed(sy, h->precision, h->flags)) return sy.L;
     // L = 32 and 64 have kernels compiled for their size
     return sy.L == 64 ? kStreamL64 : (sy.L == 32 ? kStreamL32 : -2);
@@ -345,6 +362,24 @@ int plan(mp_state* h, const mp_config* cfg) {
     const int NH = static_cast<int>((N + 1) / 2);
     int t = (static_cast<int>(h->tp_override.size()) > k && h->tp_override[k] > 0) ? h->tp_override[k]
                                                                                   : cfg->threads_per_path;
+    if (paired(h->systems[k], h->precision, h->flags)) {
+      // one CTA of cta_max threads on each half: one column of L/2 planes per thread
+      if (t != 0 && t != cta_max)
+        return fail(h, MP_EINVAL, "system %d: L=%d runs on two-CTA clusters of %d threads each", k,
+                    h->systems[k].L, cta_max);
+      tp[k] = cta_max;
+      ring[k] = 16;
+      // the ring of the CTA that owns the path holds both CTAs' warps
+      auto need = [&]() {
+        return round_up(slice_spin_offset(2 * cta_max, ring[k]) + pair_spin_bytes(kPairL, real), 128);
+      };
+      pick_ring(ring[k], slice[k], need, cta_max);
+      if (slice[k] > smem_max)
+        return fail(h, MP_EINVAL, "system %d: L=%d needs %d bytes of shared memory per CTA (max %d)", k,
+                    h->systems[k].L, slice[k], smem_max);
+      max_tp = std::max(max_tp, cta_max);
+      continue;
+    }
     if (streamed(h->systems[k], h->precision, h->flags)) {
       // one thread per column x/2 of a z-plane and about L/4 rows per thread
       const int L = h->systems[k].L, HL = L / 2;
@@ -392,6 +427,7 @@ int plan(mp_state* h, const mp_config* cfg) {
     max_tp = std::max(max_tp, t);
   }
   auto paths_per_cta = [&](int k, int cta) {
+    if (paired(h->systems[k], h->precision, h->flags)) return 1;  // one path per cluster
     int g = cta / tp[k];
     if (tp[k] > 32) g = std::min(g, 15);  // named barriers 1..15
     g = std::min<int64_t>(g, smem_max / slice[k]);
@@ -414,8 +450,16 @@ int plan(mp_state* h, const mp_config* cfg) {
   }
   if (cta < max_tp) return fail(h, MP_EINVAL, "cta_threads %d below threads per path %d", cta, max_tp);
 
+  if (cta < cta_max) {
+    for (int k = 0; k < n; ++k)
+      if (paired(h->systems[k], h->precision, h->flags))
+        return fail(h, MP_EINVAL, "cta_threads %d: L=%d runs on two-CTA clusters of %d threads each", cta,
+                    h->systems[k].L, cta_max);
+  }
+
   h->hsys.resize(n);
   h->items.clear();
+  h->pair_items.clear();
   h->spin_offset.assign(n, 0);
   int smem = 0;
   int64_t rec = 0, spins = 0;
@@ -436,7 +480,8 @@ int plan(mp_state* h, const mp_config* cfg) {
     d.beta = 1.0 / s.T;
     d.rec_offset = rec;
     d.n_paths = s.n_paths;
-    d.mode = streamed(s, h->precision, h->flags) ? kModeStreamed : kModeShared;
+    d.mode = paired(s, h->precision, h->flags) ? kModePair
+             : streamed(s, h->precision, h->flags) ? kModeStreamed : kModeShared;
     d.pad = 0;
     if (d.mode == kModeStreamed) {
       h->lattice_groups = std::max(h->lattice_groups, d.g);
@@ -447,8 +492,12 @@ int plan(mp_state* h, const mp_config* cfg) {
     h->spin_offset[k] = spins;
     spins += s.n_paths * 3 * static_cast<int64_t>(d.N);
     smem = std::max(smem, d.g * d.slice_bytes);
-    for (int64_t p0 = 0; p0 < s.n_paths; p0 += d.g)
-      h->items.push_back(WorkItem{k, static_cast<int32_t>(std::min<int64_t>(d.g, s.n_paths - p0)), p0});
+    if (d.mode == kModePair) {
+      for (int64_t p0 = 0; p0 < s.n_paths; ++p0) h->pair_items.push_back(WorkItem{k, 1, p0});
+    } else {
+      for (int64_t p0 = 0; p0 < s.n_paths; p0 += d.g)
+        h->items.push_back(WorkItem{k, static_cast<int32_t>(std::min<int64_t>(d.g, s.n_paths - p0)), p0});
+    }
     h->max_paths = std::max(h->max_paths, s.n_paths);
   }
   // largest lattices first, so the persistent CTAs finish together
@@ -465,6 +514,14 @@ int plan(mp_state* h, const mp_config* cfg) {
   if (per_sm < 1) return fail(h, MP_EINVAL, "launch shape %d threads x %d bytes does not fit an SM", cta, smem);
   h->grid = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(h->items.size()),
                                                static_cast<int64_t>(sms) * per_sm));
+  if (!h->pair_items.empty()) {
+    // a launch in clusters of two CTAs: as many clusters as can be resident
+    int clusters = 0;
+    MP_CUDA(h, sweep_cluster_occupancy(h->precision, variant, cta, smem, &clusters));
+    if (clusters < 1)
+      return fail(h, MP_EINVAL, "no two-CTA cluster of %d threads x %d bytes fits the device", cta, smem);
+    h->grid = 2 * clusters;
+  }
   return MP_OK;
 }
 
@@ -525,6 +582,9 @@ int enqueue_run(mp_state* h, int64_t s_begin, int64_t s_end, bool resume, bool s
   p.spins = h->d_spins;
   p.spin_offset = h->d_spin_offset;
   p.n_items = static_cast<int32_t>(h->items.size());
+  p.pair_items = h->d_items + h->items.size();
+  p.n_pair_items = static_cast<int32_t>(h->pair_items.size());
+  p.pair_queue = h->d_queue + 1;
   p.init_mode = h->init_mode | ((h->flags & MP_FLAG_TWO_START) ? kTwoStart : 0);
   p.key = philox_round_keys(h->seed);
   p.lattice = h->d_lattice;
@@ -550,7 +610,7 @@ int enqueue_run(mp_state* h, int64_t s_begin, int64_t s_end, bool resume, bool s
   r.n_therm = std::min(s_end, h->n_therm);
   r.n_meas = std::max<int64_t>(0, s_end - h->n_therm);
   const unsigned evflag = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
-  MP_CUDA(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int), h->stream));
+  MP_CUDA(h, cudaMemsetAsync(h->d_queue, 0, 2 * sizeof(int), h->stream));
   MP_CUDA(h, cudaMemsetAsync(h->d_error, 0, sizeof(int), h->stream));
   MP_CUDA(h, cudaEventRecordWithFlags(h->ev[0], h->stream, evflag));
   if (h->variant == kRandomSiteKernel)
@@ -585,12 +645,18 @@ int ensure_lattice(mp_state* h) {
   return MP_OK;
 }
 
-int upload_tables(mp_state* h, const std::vector<WorkItem>& items) {
+// Tables of a launch: systems, the given work items and, after them, the
+// paths for two-CTA clusters (with_pairs).
+int upload_tables(mp_state* h, const std::vector<WorkItem>& items, bool with_pairs) {
   const int n = static_cast<int>(h->hsys.size());
   MP_CUDA(h, cudaMemcpyAsync(h->d_sys, h->hsys.data(), sizeof(DevSystem) * n, cudaMemcpyHostToDevice,
                              h->stream));
-  MP_CUDA(h, cudaMemcpyAsync(h->d_items, items.data(), sizeof(WorkItem) * items.size(),
-                             cudaMemcpyHostToDevice, h->stream));
+  if (!items.empty())
+    MP_CUDA(h, cudaMemcpyAsync(h->d_items, items.data(), sizeof(WorkItem) * items.size(),
+                               cudaMemcpyHostToDevice, h->stream));
+  if (with_pairs && !h->pair_items.empty())
+    MP_CUDA(h, cudaMemcpyAsync(h->d_items + items.size(), h->pair_items.data(),
+                               sizeof(WorkItem) * h->pair_items.size(), cudaMemcpyHostToDevice, h->stream));
   MP_CUDA(h, cudaMemcpyAsync(h->d_spin_offset, h->spin_offset.data(), sizeof(int64_t) * n,
                              cudaMemcpyHostToDevice, h->stream));
   std::vector<unsigned long long> thr(10 * static_cast<size_t>(n), 0ull);
@@ -614,7 +680,7 @@ double calibrate(mp_state* h, int k) {
     paths += it.count;
     if (static_cast<int>(sub.size()) >= h->grid) break;
   }
-  if (sub.empty() || upload_tables(h, sub) != MP_OK || ensure_lattice(h) != MP_OK) return -1.0;
+  if (sub.empty() || upload_tables(h, sub, false) != MP_OK || ensure_lattice(h) != MP_OK) return -1.0;
   const double per_sweep = static_cast<double>(paths) * h->hsys[k].N;
   const int64_t sweeps = std::max<int64_t>(2, std::min<int64_t>(512, static_cast<int64_t>(2e8 / per_sweep)));
   SweepParams p{};
@@ -665,6 +731,7 @@ std::vector<int> tp_candidates(mp_state* h, int k, int cta_max) {
   };
   const int64_t N = sites_of(sy);
   const int NH = static_cast<int>((N + 1) / 2);
+  if (paired(sy, h->precision, h->flags)) return c;  // one fixed layout
   if (streamed(sy, h->precision, h->flags)) {
     const int HL = sy.L / 2;
     for (int r : {2, 4, 8}) add(std::max(HL, HL * ((sy.L + r - 1) / r)));
@@ -755,6 +822,7 @@ int check_error_flag(mp_state* h) {
   int flag = 0;
   MP_CUDA(h, cudaMemcpy(&flag, h->d_error, sizeof(int), cudaMemcpyDeviceToHost));
   if (flag == kErrCanceled) return fail(h, MP_ECANCELED, "the run was canceled; results invalid");
+  if (flag == kErrLaunch) return fail(h, MP_ECUDA, "two-CTA cluster paths ran without a cluster launch");
   if (flag) return fail(h, MP_ETIMEOUT, "a bulk copy did not complete in time; results invalid");
   return MP_OK;
 }
@@ -847,7 +915,7 @@ int mp_create_ex(const mp_config* cfg, mp_handle* out) {
   }
   rc = ensure_lattice(h);
   if (rc != MP_OK) return bail(rc);
-  rc = upload_tables(h, h->items);
+  rc = upload_tables(h, h->items, true);
   if (rc != MP_OK) return bail(rc);
   *out = h;
   return MP_OK;
@@ -977,7 +1045,7 @@ int mp_plan(mp_handle h, int* cta_threads, int* grid, int* smem_bytes, int* n_it
   if (cta_threads) *cta_threads = h->cta;
   if (grid) *grid = h->grid;
   if (smem_bytes) *smem_bytes = h->smem;
-  if (n_items) *n_items = static_cast<int>(h->items.size());
+  if (n_items) *n_items = static_cast<int>(h->items.size() + h->pair_items.size());
   return MP_OK;
 }
 
@@ -1148,7 +1216,7 @@ int mp_system_plan(mp_handle h, int system, int* threads_per_path, int* paths_pe
   const DevSystem& d = h->hsys[system];
   if (threads_per_path) *threads_per_path = d.tp;
   if (paths_per_cta) *paths_per_cta = d.g;
-  if (streamed_from_hbm) *streamed_from_hbm = d.mode == kModeStreamed ? 1 : 0;
+  if (streamed_from_hbm) *streamed_from_hbm = d.mode;  // 0 shared memory, 1 HBM, 2 two-CTA cluster
   return MP_OK;
 }
 

@@ -415,19 +415,26 @@ struct Meter {
   // j % R, kept in a 32-bit counter that advances one sweep at a time (no
   // 64-bit division per sweep); start() sets it for j_first
   int cur = 0;
+  // partial sums per sweep (one per warp of the path: nwarps, or twice that
+  // when two CTAs of a cluster hold the lattice), and the first of them this
+  // CTA's warps write (the partner CTA writes into the owner's ring)
+  int nslot = 0, slot_off = 0;
 
-  __device__ void start() { cur = static_cast<int>(((j_first / R) & 1) * R + j_first % R); }
-  __device__ Real* slot(int64_t j) const {
-    return red + ((((j / R) & 1) * R + (j % R)) * nwarps) * kRedSlots;
+  __device__ void start() {
+    if (nslot == 0) nslot = nwarps;
+    cur = static_cast<int>(((j_first / R) & 1) * R + j_first % R);
   }
-  __device__ Real* cur_slot() const { return red + (cur * nwarps) * kRedSlots; }
+  __device__ Real* slot(int64_t j) const {
+    return red + ((((j / R) & 1) * R + (j % R)) * nslot) * kRedSlots;
+  }
+  __device__ Real* cur_slot() const { return red + (cur * nslot) * kRedSlots; }
   __device__ void advance() {
     if (++cur == 2 * R) cur = 0;
   }
   // Per-site observables (Sec. 2.2) of one measurement sweep from its slot.
   __device__ void observe(const Real* sl, Real& e, Real& ex, Real& ey, Real& ez) const {
     Real E = Real(0), MX = Real(0), MY = Real(0), MZ = Real(0);
-    for (int w = 0; w < nwarps; ++w) {
+    for (int w = 0; w < nslot; ++w) {
       E += sl[w * kRedSlots + 0];
       MX += sl[w * kRedSlots + 1];
       MY += sl[w * kRedSlots + 2];
@@ -451,7 +458,7 @@ struct Meter {
       part.mz += A::shfl(part.mz, o);
     }
     if (lane == 0) {
-      Real* r = cur_slot() + warp * kRedSlots;
+      Real* r = cur_slot() + (slot_off + warp) * kRedSlots;
       r[0] = part.eb;
       r[1] = part.mx;
       r[2] = part.my;
@@ -730,6 +737,271 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
     }
   }
   group_sync(tp, bar);  // the slice is reused by the next item
+}
+
+// ------------------------------------------------ two-CTA clusters -------
+// A simple cubic lattice too large for one SM's shared memory but not for
+// two (FP32 L = 32: 393 KB of spins) is held by the two CTAs of a cluster:
+// CTA rank r keeps the z-planes r L/2 .. r L/2 + L/2 - 1, and in each colour
+// array also one halo plane on either side (local planes 0 and L/2 + 1) with
+// the partner's boundary plane.  A half-sweep of colour c updates the local
+// planes by the same column walk as run_path (the halo planes give the +-z
+// neighbours across the cut, so no index wraps in z), and each thread pushes
+// the new values of its column's two boundary sites straight into the
+// partner's halo planes of colour c (distributed shared memory stores).  The
+// partner reads colour c only in the next half-sweep, after the cluster
+// barrier that ends this one, so one barrier per half-sweep orders
+// everything; during a half-sweep each CTA reads only colour 1 - c and writes
+// only colour c.  Measurement partials of the partner's warps go into the
+// owner's (rank 0's) partial-sum ring, which then holds every warp of the
+// lattice; rank 0 flushes, keeps the FP64 accumulators and writes the record.
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_size() {
+  uint32_t n;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(n));
+  return n;
+}
+// Generic address of the same shared-memory location in CTA `rank` of the cluster.
+template <typename T>
+__device__ __forceinline__ T* map_rank(T* p, uint32_t rank) {
+  uint64_t out;
+  asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"(reinterpret_cast<uint64_t>(p)), "r"(rank));
+  return reinterpret_cast<T*>(out);
+}
+// Every thread of both CTAs; release/acquire at cluster scope, so shared
+// memory written (locally or remotely) before it is visible after it.
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+template <int L>
+struct PairGeom {
+  static constexpr int HL = L / 2, HP = L * L / 2;
+  static constexpr int ZL = L / 2;       // planes per CTA
+  static constexpr int S = HP * (ZL + 2);  // sites per colour array, with the two halo planes
+  static_assert(6 * S * 4 == pair_spin_bytes(L, 4), "pair layout");
+};
+
+// Planes of a column walked per unrolled chunk: the mixed-size kernel that
+// holds this walk stays within 128 registers without spills at 4 (8 spills).
+constexpr int kPairChunk = 4;
+
+template <typename Real, int L, bool kMeas, bool kEnergy>
+__device__ __forceinline__ void half_sweep_pair(int c, int zbase, const PhiloxPrefix& pre,
+                                                const PhiloxKeys& key, Real* sp, Real* partner_sp,
+                                                int tid, int tp, Real J, Real hf, Real bp,
+                                                int& accepted, Partials<Real>& part) {
+  using G = PairGeom<L>;
+  constexpr int HL = G::HL, HP = G::HP, ZL = G::ZL, S = G::S;
+  const SpinView<Real> own(sp + c * 3 * S, S), oth(sp + (1 - c) * 3 * S, S);
+  const SpinView<Real> halo(partner_sp + c * 3 * S, S);  // the partner's array of colour c
+  for (int col = tid; col < HP; col += tp) {
+    const int hx = col % HL;
+    const int y = col / HL;
+    const int oyp = (y == L - 1) ? -(L - 1) * HL : HL;
+    const int oym = (y == 0) ? (L - 1) * HL : -HL;
+    const int oxp1 = (hx == HL - 1) ? -(HL - 1) : 1;  // +x offset when x is odd
+    const int oxm0 = (hx == 0) ? (HL - 1) : -1;         // -x offset when x is even
+    int hh = col + HP;                                   // local plane 1
+    V3<Real> o0 = oth.ld(hh);       // the other colour at the site's half index
+    V3<Real> mz = oth.ld(hh - HP);  // -z neighbour (halo plane 0)
+#pragma unroll(kPairChunk)
+    for (int zl = 1; zl <= ZL; ++zl, hh += HP) {
+      // global plane zbase + zl - 1
+      const int p = (y + zbase + zl - 1 + c) & 1;
+      const int nxo = hh + (p ? oxp1 : oxm0);
+      const V3<Real> cz = oth.ld(hh + HP);
+      const V3<Real> f =
+          add3(add3(add3(add3(add3(o0, oth.ld(nxo)), oth.ld(hh + oyp)), oth.ld(hh + oym)), cz), mz);
+      // site index x + L(y + L z_global) = 2 (col + HP z_global) + p
+      update<Real, kMeas, kEnergy>(static_cast<uint32_t>(2 * (hh + HP * (zbase - 1)) + p), pre, key,
+                                   own, hh, f.x, f.y, f.z, J, hf, bp, accepted, part);
+      mz = o0;
+      o0 = cz;
+    }
+    // the column's boundary sites to the partner's halo planes: local plane 1
+    // is the partner's plane ZL + 1, local plane ZL its plane 0
+    const V3<Real> a = own.ld(col + HP);
+    halo.st(col + HP * (ZL + 1), a.x, a.y, a.z);
+    const V3<Real> b = own.ld(col + HP * ZL);
+    halo.st(col, b.x, b.y, b.z);
+  }
+}
+
+// One path of a simple cubic L (= kPairL) lattice on the two CTAs of a
+// cluster; every thread of both CTAs calls it with the same arguments except
+// `rank` and tid.  The record, the saved accumulators and the acceptance
+// count are written by rank 0; each rank saves and outputs its own planes.
+template <typename Real, int L>
+__device__ void run_path_pair(const DevSystem& sy, int sys_idx, int64_t path, const SweepParams& P,
+                              unsigned char* slice, int tid, int tp, uint32_t rank) {
+  using A = Arith<Real>;
+  using G = PairGeom<L>;
+  constexpr int HL = G::HL, HP = G::HP, ZL = G::ZL, S = G::S;
+  constexpr int NH = L * L * L / 2;  // sites per colour of the whole lattice
+  // rank 0's ring holds the partials of both CTAs' warps
+  Real* sp = reinterpret_cast<Real*>(slice + slice_spin_offset(2 * tp, sy.ring));
+  Real* partner_sp = map_rank(sp, rank ^ 1u);
+  const int zbase = static_cast<int>(rank) * ZL;
+  const uint32_t c2 = static_cast<uint32_t>(path);
+  const uint32_t c3u = kTagUpdate | (static_cast<uint32_t>(sys_idx) << 8);
+  const uint32_t c3i = kTagInit | (static_cast<uint32_t>(sys_idx) << 8);
+  const int init = path_init_mode(P.init_mode, path, sy.n_paths);
+  const Real J = static_cast<Real>(sy.J), hf = static_cast<Real>(sy.h);
+  const Real bp = A::beta_param(sy.beta);
+  const int64_t j_first = P.s_begin > P.n_therm ? P.s_begin - P.n_therm : 0;
+  Real* red0 = reinterpret_cast<Real*>(slice + slice_red_offset());
+  Meter<Real> meter{reinterpret_cast<double*>(slice + slice_acc_offset()),
+                    rank == 0 ? red0 : map_rank(red0, 0u),
+                    sy.ring, tp >> 5, tid & 31, tid >> 5, tid,
+                    1.0 / static_cast<double>(sy.N), J, hf, j_first};
+  meter.nslot = 2 * (tp >> 5);
+  meter.slot_off = rank == 0 ? 0 : (tp >> 5);
+  meter.start();
+  unsigned char* st = path_state(P, sys_idx, path);
+  Real* st_spins = st ? reinterpret_cast<Real*>(st + kStateHeader) : nullptr;
+  __shared__ int pair_cancel;
+  __shared__ double pair_xch[2];  // rank 1's acceptance count and worst | |S| - 1 |, on rank 0
+  const bool resume = P.resume && st;
+
+  // local plane zl holds global plane (zbase + zl - 1) mod L, zl = 0 .. ZL + 1
+  for (int c = 0; c < 2; ++c) {
+    const SpinView<Real> own(sp + c * 3 * S, S);
+    for (int h = tid; h < S; h += tp) {
+      const int col = h % HP, zl = h / HP;
+      const int zg = (zbase + zl - 1 + L) % L;
+      const int hg = col + HP * zg;  // half index in the whole lattice
+      Real x, y, z;
+      if (resume) {
+        const SpinView<Real> saved(st_spins + c * 3 * NH, NH);
+        const V3<Real> v = saved.ld(hg);
+        x = v.x;
+        y = v.y;
+        z = v.z;
+      } else {
+        const int p = (col / HL + zg + c) & 1;
+        initial_spin<Real>(static_cast<uint32_t>(2 * hg + p), c2, c3i, P, init, x, y, z);
+      }
+      own.st(h, x, y, z);
+    }
+  }
+  if (tid < kAccDoubles) meter.acc[tid] = (resume && rank == 0) ? reinterpret_cast<const double*>(st)[tid] : 0.0;
+  const double accepted_before = (resume && rank == 0) ? reinterpret_cast<const double*>(st)[kAccDoubles] : 0.0;
+  if (tid == 0) pair_cancel = 0;
+  cluster_sync_all();
+
+  int accepted = 0;
+  bool canceled = false;
+  for (int64_t s = P.s_begin; s < P.s_end; ++s) {
+    const uint32_t sw = static_cast<uint32_t>(s);
+    const PhiloxPrefix pre = philox_prefix(sw, c2, c3u, P.key);
+    Partials<Real> part{Real(0), Real(0), Real(0), Real(0)};
+    // rank 0 polls the host's flag and tells both CTAs, so that they stop together
+    if (rank == 0 && tid == 0 && P.cancel != nullptr && ((s - P.s_begin) % kCancelPoll) == 0 &&
+        *P.cancel != 0) {
+      pair_cancel = 1;
+      *map_rank(&pair_cancel, 1u) = 1;
+      atomicExch(P.error, kErrCanceled);
+    }
+    const bool meas = s >= P.n_therm;
+    if (meas)
+      half_sweep_pair<Real, L, true, false>(0, zbase, pre, P.key, sp, partner_sp, tid, tp, J, hf, bp,
+                                            accepted, part);
+    else
+      half_sweep_pair<Real, L, false, false>(0, zbase, pre, P.key, sp, partner_sp, tid, tp, J, hf, bp,
+                                             accepted, part);
+    cluster_sync_all();
+    if (pair_cancel) {
+      canceled = true;
+      break;
+    }
+    if (meas) {
+      if (rank == 0) meter.maybe_flush(s - P.n_therm);
+      half_sweep_pair<Real, L, true, true>(1, zbase, pre, P.key, sp, partner_sp, tid, tp, J, hf, bp,
+                                           accepted, part);
+      meter.record(part);
+    } else {
+      half_sweep_pair<Real, L, false, false>(1, zbase, pre, P.key, sp, partner_sp, tid, tp, J, hf, bp,
+                                             accepted, part);
+    }
+    cluster_sync_all();
+  }
+  if (canceled) {  // the call is discarded: no record, no saved state
+    cluster_sync_all();
+    return;
+  }
+  const int64_t n_meas_done = P.s_end > P.n_therm ? P.s_end - P.n_therm : 0;
+  if (rank == 0) meter.finish(n_meas_done);
+  __syncthreads();  // the ring area is free from here on (finish has read its last slot)
+
+  // this CTA's planes: worst | |S| - 1 |, saved state, final spins
+  Real worst = Real(0);
+  for (int c = 0; c < 2; ++c) {
+    const SpinView<Real> own(sp + c * 3 * S, S);
+    for (int h = tid + HP; h < HP * (ZL + 1); h += tp) {
+      const V3<Real> v = own.ld(h);
+      worst = fmax(worst, fabs(sqrt(v.x * v.x + v.y * v.y + v.z * v.z) - Real(1)));
+      const int col = h % HP, zg = zbase + h / HP - 1;
+      const int hg = col + HP * zg;
+      if (P.save && st) SpinView<Real>(st_spins + c * 3 * NH, NH).st(hg, v.x, v.y, v.z);
+      if (P.spins != nullptr) {
+        const int i = 2 * hg + ((col / HL + zg + c) & 1);
+        double* out = P.spins + P.spin_offset[sys_idx] + path * 3 * static_cast<int64_t>(sy.N) + 3 * i;
+        out[0] = v.x;
+        out[1] = v.y;
+        out[2] = v.z;
+      }
+    }
+  }
+  // acceptance count and worst norm of this CTA; rank 1 hands its totals to rank 0
+  double nacc = static_cast<double>(accepted), wst = static_cast<double>(worst);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    nacc += __shfl_xor_sync(0xffffffffu, nacc, o);
+    wst = fmax(wst, __shfl_xor_sync(0xffffffffu, wst, o));
+  }
+  double* pair_red = reinterpret_cast<double*>(red0);  // this CTA's own ring area
+  if ((tid & 31) == 0) {
+    pair_red[2 * (tid >> 5)] = nacc;
+    pair_red[2 * (tid >> 5) + 1] = wst;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double tot = 0.0, wmax = 0.0;
+    for (int w = 0; w < (tp >> 5); ++w) {
+      tot += pair_red[2 * w];
+      wmax = fmax(wmax, pair_red[2 * w + 1]);
+    }
+    if (rank == 1) {
+      double* x = map_rank(pair_xch, 0u);
+      x[0] = tot;
+      x[1] = wmax;
+    } else {
+      pair_red[0] = tot;
+      pair_red[1] = wmax;
+    }
+  }
+  cluster_sync_all();  // rank 1's totals are in rank 0's pair_xch
+  if (rank == 0 && tid == 0) {
+    const double tot = accepted_before + pair_red[0] + pair_xch[0];
+    const double wmax = fmax(pair_red[1], pair_xch[1]);
+    double* rec = P.records + (sy.rec_offset + path) * MP_NREC;
+    const double inv = n_meas_done > 0 ? 1.0 / static_cast<double>(n_meas_done) : NAN;
+    for (int k = MP_R_E; k <= MP_R_MMZ; ++k) rec[k] = meter.acc[k] * inv;
+    for (int k = MP_R_FMX; k <= MP_R_FE; ++k) rec[k] = meter.acc[k];
+    rec[MP_R_ACC] = tot / (static_cast<double>(P.s_end) * static_cast<double>(sy.N));
+    rec[MP_R_NORM] = wmax;
+    rec[MP_R_SPARE] = 0.0;
+    if (P.save && st) {
+      for (int k = 0; k < kAccDoubles; ++k) reinterpret_cast<double*>(st)[k] = meter.acc[k];
+      reinterpret_cast<double*>(st)[kAccDoubles] = tot;
+    }
+  }
+  cluster_sync_all();  // the slices (and pair_xch) are reused by the next item
 }
 
 // ------------------------------------------------------ TMA primitives --
@@ -1112,6 +1384,33 @@ __global__ void __launch_bounds__(CtaLimit<Real, kLattice>::value, 1)
     sweep_kernel(const SweepParams P) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_item;
+  if constexpr (kLattice == kMixedKernel && sizeof(Real) == 4) {
+    // First the lattices held by two CTAs: the cluster takes one path at a
+    // time from its own queue (rank 0 draws, both CTAs read), then each CTA
+    // goes on to the single-CTA items below.
+    if (P.n_pair_items > 0) {
+      if (cluster_size() != 2) {
+        if (threadIdx.x == 0) atomicExch(P.error, kErrLaunch);
+      } else {
+        __shared__ int s_pair;
+        const uint32_t rank = cluster_rank();
+        for (;;) {
+          if (rank == 0 && threadIdx.x == 0) {
+            const int it = atomicAdd(P.pair_queue, 1);
+            s_pair = it;
+            *map_rank(&s_pair, 1u) = it;
+          }
+          cluster_sync_all();
+          const int item = s_pair;
+          cluster_sync_all();  // both CTAs have read the item before rank 0 draws again
+          if (item >= P.n_pair_items) break;
+          const WorkItem it = P.pair_items[item];
+          run_path_pair<Real, kPairL>(P.systems[it.sys], it.sys, it.path0, P, smem,
+                                      static_cast<int>(threadIdx.x), static_cast<int>(blockDim.x), rank);
+        }
+      }
+    }
+  }
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_item = atomicAdd(P.queue, 1);

@@ -57,12 +57,46 @@ cudaError_t SUFFIX(sweep_occupancy)(int variant, int cta, int smem, int* blocks)
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, cta, smem);
 }
 
+// Launch of a variant; with paths for two-CTA clusters (p.n_pair_items > 0)
+// the grid (then even) runs as clusters of two CTAs.
 cudaError_t SUFFIX(launch_sweep)(int variant, const SweepParams& p, int grid, int cta, int smem,
                                  cudaStream_t st) {
   const void* k = kernel_of(variant);
   if (!k) return cudaErrorInvalidValue;
   void* args[] = {const_cast<SweepParams*>(&p)};
-  return cudaLaunchKernel(k, dim3(grid), dim3(cta), args, static_cast<size_t>(smem), st);
+  if (p.n_pair_items <= 0)
+    return cudaLaunchKernel(k, dim3(grid), dim3(cta), args, static_cast<size_t>(smem), st);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(cta);
+  cfg.dynamicSmemBytes = static_cast<size_t>(smem);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, k, args);
+}
+
+// Two-CTA clusters of a variant that can be resident at once.
+cudaError_t SUFFIX(sweep_cluster_occupancy)(int variant, int cta, int smem, int* clusters) {
+  const void* k = kernel_of(variant);
+  if (!k) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2);
+  cfg.blockDim = dim3(cta);
+  cfg.dynamicSmemBytes = static_cast<size_t>(smem);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaOccupancyMaxActiveClusters(clusters, k, &cfg);
 }
 
 }  // namespace mpk
