@@ -11,10 +11,12 @@
  *
  * Model (Sec. 2.1): H = -(J/2) sum_n sum_lambda S_n . S_{n+lambda} - h sum_n S^z_n,
  * Eq. (1) plus a Zeeman term (h = 0 is the paper's model), unit spins of Eq. (2),
- * on a periodic simple-cubic lattice of N = L^3 sites (L even; L <= 26 in FP32
- * and L <= 20 in FP64 run with the lattice in shared memory, larger lattices
- * are streamed from HBM while their half-plane ring fits in shared memory:
- * L <= 64 in FP32, L <= 44 in FP64) or an open chain of N = L spins.
+ * on a periodic simple-cubic lattice of N = L^3 sites (L even, at most 1024;
+ * L <= 26 in FP32 and L <= 20 in FP64 run with the lattice in shared memory,
+ * FP32 L = 32 in the shared memory of a two-CTA cluster, larger lattices are
+ * streamed from HBM while their half-plane ring fits in shared memory: L <= 64
+ * in FP32, L <= 44 in FP64, and updated in place in HBM beyond that) or an
+ * open chain of N = L spins.
  *
  * Conventions shared by every call:
  *   - Every function returns an int status (MP_OK or a negative MP_E* code),
@@ -332,10 +334,12 @@ int mp_cancel(mp_handle h);
 
 /* Launch shape of one system: threads per path, paths per CTA, and where
  * its lattice lives during a run: 0 in one CTA's shared memory, 1 streamed
- * from HBM, 2 split over the shared memory of the two CTAs of a cluster
- * (FP32 simple cubic L = 32: each CTA holds half of the z-planes, one path
- * per cluster, threads_per_path then counts one CTA).  Any output may be
- * NULL.  Errors: MP_EINVAL (bad index). */
+ * from HBM through shared-memory half-plane buffers, 2 split over the shared
+ * memory of the two CTAs of a cluster (FP32 simple cubic L = 32: each CTA
+ * holds half of the z-planes, one path per cluster, threads_per_path then
+ * counts one CTA), 3 updated in place in HBM (lattices whose half-plane ring
+ * does not fit: FP64 L >= 46, FP32 L >= 66).  Any output may be NULL.
+ * Errors: MP_EINVAL (bad index). */
 int mp_system_plan(mp_handle h, int system, int* threads_per_path, int* paths_per_cta,
                    int* streamed_from_hbm);
 

@@ -358,7 +358,7 @@ class Simulation:
         v = [ctypes.c_int() for _ in range(3)]
         _check(_lib.mp_system_plan(self._h, system, *[ctypes.byref(x) for x in v]), self._h)
         return dict(threads_per_path=v[0].value, paths_per_cta=v[1].value, streamed=v[2].value == 1,
-                    cluster_pair=v[2].value == 2)
+                    cluster_pair=v[2].value == 2, in_place_hbm=v[2].value == 3)
 
 
 def _wrap_device(ptr: int, shape, device):

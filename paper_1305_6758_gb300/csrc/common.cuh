@@ -39,13 +39,16 @@ struct DevSystem {
   double T, J, h, beta;
   int64_t rec_offset;   // global index of this system's path 0
   int64_t n_paths;
-  int32_t mode;         // kModeShared: lattice in shared memory; kModeStreamed: in HBM
+  int32_t mode;         // kModeShared / kModeStreamed / kModePair / kModeGlobal
   int32_t pad;
 };
 
 constexpr int kModeShared = 0;
 constexpr int kModeStreamed = 1;
 constexpr int kModePair = 2;  // held in the shared memory of the two CTAs of a cluster
+constexpr int kModeGlobal = 3;  // updated in place in HBM (too large for a half-plane ring)
+// The sweep-kernel variant of batches whose lattices are all updated in place.
+constexpr int kGlobalKernel = -5;
 // The lattice size held by two-CTA clusters (FP32 simple cubic L = 32: 393 KB
 // of spins), and the shared-memory bytes of one CTA's half with its two halo
 // planes per colour: 2 colours x (L/2 + 2) planes x L^2/2 sites x 3 values.

@@ -121,6 +121,17 @@ bool streamed(const mp_system& s, int precision, uint32_t flags) {
          ((flags & MP_FLAG_STREAM) || !sweep_supports_L(precision, s.L));
 }
 
+// Lattices to stream whose ring of nine half-planes does not fit one SM's
+// shared memory (FP64 L >= 46, FP32 L >= 66; `optin` is the device's largest
+// shared memory per CTA, of which the kernels' static data take under 4 KB)
+// are updated in place in HBM instead: every site decoded from its index,
+// neighbours read from global memory, one barrier per half-sweep.
+bool in_place(const mp_system& s, int precision, uint32_t flags, int optin) {
+  if (!streamed(s, precision, flags)) return false;
+  const int real = precision == MP_FP64 ? 8 : 4;
+  return 128 + 9 * half_plane_bytes(s.L, real) + slice_spin_offset(32, 1) > optin - 4096;
+}
+
 }  // namespace
 
 struct mp_state {
@@ -312,12 +323,16 @@ int plan(mp_state* h, const mp_config* cfg) {
   h->max_paths = 0;
   // one kernel per lattice size when the batch has a single size; lattices
   // too large for shared memory are streamed from HBM (any size, one kernel)
+  int optin = 0;
+  MP_CUDA(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+  auto global = [&](const mp_system& sy) { return in_place(sy, h->precision, h->flags, optin); };
   // lattices held by two-CTA clusters run in the mixed-size kernel
   auto variant_of = [&](const mp_system& sy) {
     if (sy.lattice == MP_LATTICE_ISING) return kIsingKernel;
     if (sy.lattice == MP_LATTICE_CHAIN) return -1;
     if (paired(sy, h->precision, h->flags)) return 0;  // the mixed-size kernel
     if (!streamed(sy, h->precision, h->flags)) return sy.L;
+    if (global(sy)) return kGlobalKernel;
     // L = 32 and 64 have kernels compiled for their size
     return sy.L == 64 ? kStreamL64 : (sy.L == 32 ? kStreamL32 : -2);
   };
@@ -325,10 +340,11 @@ int plan(mp_state* h, const mp_config* cfg) {
   bool all_streamed = true;
   for (int k = 0; k < n; ++k) {
     const int v = variant_of(h->systems[k]);
-    all_streamed = all_streamed && (v == -2 || v == kStreamL64 || v == kStreamL32);
+    all_streamed = all_streamed && (v == -2 || v == kStreamL64 || v == kStreamL32 || v == kGlobalKernel);
     if (v != variant) variant = 0;
   }
-  if (variant == 0 && all_streamed) variant = -2;  // streamed sizes mixed: one streamed kernel
+  // streamed sizes mixed, or streamed with in-place ones: the streamed kernel runs both
+  if (variant == 0 && all_streamed) variant = -2;
   h->variant = variant;
   int sms = 0, smem_max = 0, cta_max = 0;
   MP_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
@@ -378,6 +394,16 @@ int plan(mp_state* h, const mp_config* cfg) {
         return fail(h, MP_EINVAL, "system %d: L=%d needs %d bytes of shared memory per CTA (max %d)", k,
                     h->systems[k].L, slice[k], smem_max);
       max_tp = std::max(max_tp, cta_max);
+      continue;
+    }
+    if (global(h->systems[k])) {
+      // in place in HBM: one CTA's worth of threads per path by default
+      if (t == 0) t = cta_max;
+      if (t > cta_max) return fail(h, MP_EINVAL, "threads_per_path %d above %d", t, cta_max);
+      tp[k] = t;
+      ring[k] = 16;
+      pick_ring(ring[k], slice[k], [&]() { return round_up(slice_spin_offset(t, ring[k]), 128); }, t);
+      max_tp = std::max(max_tp, t);
       continue;
     }
     if (streamed(h->systems[k], h->precision, h->flags)) {
@@ -481,12 +507,16 @@ int plan(mp_state* h, const mp_config* cfg) {
     d.rec_offset = rec;
     d.n_paths = s.n_paths;
     d.mode = paired(s, h->precision, h->flags) ? kModePair
+             : global(s)                         ? kModeGlobal
              : streamed(s, h->precision, h->flags) ? kModeStreamed : kModeShared;
     d.pad = 0;
     if (d.mode == kModeStreamed) {
       h->lattice_groups = std::max(h->lattice_groups, d.g);
       h->lattice_stride = std::max<int64_t>(
           h->lattice_stride, static_cast<int64_t>(2) * s.L * half_plane_bytes(s.L, real));
+    } else if (d.mode == kModeGlobal) {  // the shared-memory layout, in HBM
+      h->lattice_groups = std::max(h->lattice_groups, d.g);
+      h->lattice_stride = std::max<int64_t>(h->lattice_stride, lattice_bytes(s, real));
     }
     rec += s.n_paths;
     h->spin_offset[k] = spins;
@@ -1216,7 +1246,8 @@ int mp_system_plan(mp_handle h, int system, int* threads_per_path, int* paths_pe
   const DevSystem& d = h->hsys[system];
   if (threads_per_path) *threads_per_path = d.tp;
   if (paths_per_cta) *paths_per_cta = d.g;
-  if (streamed_from_hbm) *streamed_from_hbm = d.mode;  // 0 shared memory, 1 HBM, 2 two-CTA cluster
+  // 0 shared memory, 1 streamed from HBM, 2 two-CTA cluster, 3 in place in HBM
+  if (streamed_from_hbm) *streamed_from_hbm = d.mode;
   return MP_OK;
 }
 

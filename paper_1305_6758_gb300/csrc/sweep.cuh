@@ -172,6 +172,36 @@ struct GeomSC {
   }
 };
 
+// Periodic simple cubic lattice of run-time L (even), every site decoded from
+// its half index (neighbours in the same fixed order as GeomSC): the geometry
+// of lattices updated in place in HBM, which are too large for a ring of
+// half-planes in shared memory.
+struct GeomSCDyn {
+  int L;
+  static constexpr int NNB = 6;
+  static constexpr bool kColumns = false;
+  __device__ __forceinline__ int count(int) const { return L * L * L / 2; }
+  __device__ __forceinline__ int stride() const { return L * L * L / 2; }
+  __device__ __forceinline__ int site(int h, int c, int* nb, int& nn) const {
+    const int HL = L / 2, HP = L * L / 2;
+    const int hx = h % HL;
+    const int t = h / HL;
+    const int y = t % L;
+    const int z = t / L;
+    const int p = (y + z + c) & 1;
+    const int x = 2 * hx + p;
+    const int hrow = h - hx;
+    nb[0] = hrow + ((x + 1 == L) ? 0 : ((x + 1) >> 1));
+    nb[1] = hrow + ((x == 0) ? ((L - 1) >> 1) : ((x - 1) >> 1));
+    nb[2] = (y == L - 1) ? h - (L - 1) * HL : h + HL;
+    nb[3] = (y == 0) ? h + (L - 1) * HL : h - HL;
+    nb[4] = (z == L - 1) ? h - (L - 1) * HP : h + HP;
+    nb[5] = (z == 0) ? h + (L - 1) * HP : h - HP;
+    nn = 6;
+    return 2 * h + p;
+  }
+};
+
 // Open chain of N spins: colour i mod 2, neighbours i-1 then i+1 where they exist.
 struct GeomChain {
   int N;
@@ -595,12 +625,14 @@ __device__ __forceinline__ void poll_cancel(const SweepParams& P, int64_t s, int
 }
 
 // ------------------------------------------------------------- one path --
+// The lattice lives in the slice's shared memory, or in HBM at `hbm_spins`
+// (the same layout) when it is updated in place there.
 template <typename Real, class Geom>
 __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, int sys_idx,
                                          int64_t path, const SweepParams& P, unsigned char* slice,
-                                         int tid, int tp, int bar) {
+                                         int tid, int tp, int bar, Real* hbm_spins = nullptr) {
   using A = Arith<Real>;
-  Real* sp = reinterpret_cast<Real*>(slice + slice_spin_offset(tp, sy.ring));
+  Real* sp = hbm_spins ? hbm_spins : reinterpret_cast<Real*>(slice + slice_spin_offset(tp, sy.ring));
   const int S = geo.stride();
   const uint32_t c2 = static_cast<uint32_t>(path);
   const uint32_t c3u = kTagUpdate | (static_cast<uint32_t>(sys_idx) << 8);
@@ -1438,8 +1470,19 @@ __global__ void __launch_bounds__(CtaLimit<Real, kLattice>::value, 1)
           run_path_streamed<Real, kL, 0>(sy, it.sys, it.path0 + g, P, smem + g * sy.slice_bytes,
                                          tid, sy.tp, 1 + g, lat);
         done = true;
-      } else if constexpr (kLattice == kStreamKernel || kLattice == kMixedKernel) {
-        if (sy.mode == kModeStreamed) {
+      }
+      if constexpr (kLattice == kStreamKernel || kLattice == kMixedKernel || kLattice == kGlobalKernel) {
+        if (!done && sy.mode == kModeGlobal) {
+          Real* lat = reinterpret_cast<Real*>(
+              static_cast<unsigned char*>(P.lattice) +
+              (static_cast<int64_t>(blockIdx.x) * P.lattice_groups + g) * P.lattice_stride);
+          run_path<Real>(GeomSCDyn{sy.L}, sy, it.sys, it.path0 + g, P, smem + g * sy.slice_bytes, tid,
+                         sy.tp, 1 + g, lat);
+          done = true;
+        }
+      }
+      if constexpr (kLattice == kStreamKernel || kLattice == kMixedKernel) {
+        if (!done && sy.mode == kModeStreamed) {
           Real* lat = reinterpret_cast<Real*>(
               static_cast<unsigned char*>(P.lattice) +
               (static_cast<int64_t>(blockIdx.x) * P.lattice_groups + g) * P.lattice_stride);

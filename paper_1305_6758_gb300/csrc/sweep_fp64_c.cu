@@ -11,6 +11,7 @@ const void* SUFFIX(sweep_part_c)(int variant) {
   switch (variant) {
     MPK_PART_CASE(kChainKernel)
     MPK_PART_CASE(kStreamKernel)
+    MPK_PART_CASE(kGlobalKernel)
     MPK_PART_CASE(stream_variant(32))
     MPK_PART_CASE(stream_variant(64))
     default: return nullptr;

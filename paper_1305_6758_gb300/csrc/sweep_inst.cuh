@@ -16,8 +16,9 @@ __device__ __forceinline__ void dispatch_path(const DevSystem& sy, int sys_idx, 
                                               int tp, int bar) {
   if constexpr (kLattice > 0) {
     run_path<Real>(GeomSC<kLattice>{}, sy, sys_idx, path, P, slice, tid, tp, bar);
-  } else if constexpr (kLattice == kStreamKernel || stream_variant_L(kLattice) > 0) {
-    // streamed paths are run by the kernel itself; nothing in shared memory only
+  } else if constexpr (kLattice == kStreamKernel || kLattice == kGlobalKernel ||
+                       stream_variant_L(kLattice) > 0) {
+    // streamed and in-place paths are run by the kernel itself; nothing in shared memory only
   } else if constexpr (kLattice == kChainKernel) {
     run_path<Real>(GeomChain{sy.N}, sy, sys_idx, path, P, slice, tid, tp, bar);
   } else {

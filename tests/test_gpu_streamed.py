@@ -123,10 +123,33 @@ def test_stalled_bulk_copy_reports_timeout():
         assert np.isfinite(ok.estimates(0)["e"])
 
 
-def test_fp64_l64_does_not_fit_the_ring():
-    with pytest.raises(mp.MPError) as ei:
-        mp.Simulation([mp.System(64, 1.44, n_paths=1)], 1, 1, precision=mp.FP64)
-    assert ei.value.status == mp.MP_EINVAL
+@pytest.mark.parametrize("systems", [
+    [mp.System(64, 1.44, n_paths=2)],                                      # the in-place kernel
+    [mp.System(46, 0.9, h=0.05, n_paths=2), mp.System(8, 1.0, n_paths=3)],  # with a shared-memory size
+    [mp.System(46, 1.2, J=-1.0, n_paths=2), mp.System(24, 1.1, n_paths=2)],  # with a streamed size
+])
+def test_in_place_fp64_matches_oracle(systems):
+    """FP64 lattices whose half-plane ring does not fit shared memory (L >= 46)
+    are updated in place in HBM: path by path equal to the oracle."""
+    with mp.Simulation(systems, 1, 2, seed=5, precision=mp.FP64) as sim:
+        sim.run()
+        recs = [sim.paths(k) for k in range(len(systems))]
+        assert sim.system_plan(0)["in_place_hbm"]
+    refs = O.run([osys(s) for s in systems], 1, 2, seed=5)
+    for g, r in zip(recs, refs):
+        np.testing.assert_allclose(g[:, FIELDS], r[:, FIELDS], rtol=1e-10, atol=1e-13)
+        np.testing.assert_array_equal(g[:, 17], r[:, 17])
+
+
+def test_in_place_fp32_l66_against_oracle():
+    systems = [mp.System(66, 1.44, n_paths=2)]
+    with mp.Simulation(systems, 0, 1, seed=7) as sim:
+        sim.run()
+        got = sim.paths(0)
+        assert sim.system_plan(0)["in_place_hbm"]
+    ref = O.run([osys(systems[0])], 0, 1, seed=7)[0]
+    bad = sum(int(np.max(np.abs(g[FIELDS] - r[FIELDS])) > 1e-5) for g, r in zip(got, ref))
+    assert bad <= 1
 
 
 def test_autotune_changes_only_the_launch_shape():
@@ -162,7 +185,7 @@ def test_autotune_choice_is_remembered_for_the_same_batch_shape():
 
 def test_fp32_batched_form_against_the_oracle():
     """The batched workload's shape in FP32: uneven sizes in one persistent
-    launch, L = 32 streamed, autotuned. Every system's <e> and <|m|> are
+    launch, L = 32 on two-CTA clusters, autotuned. Every system's <e> and <|m|> are
     within 3 combined standard errors of the FP64 oracle, and <e> is within
     1e-4 (plus 3 standard errors) of the FP64 GPU form from the same starts."""
     sizes = ((8, 512), (12, 256), (16, 128), (20, 64), (24, 32), (32, 16))
