@@ -33,7 +33,7 @@ struct NoallocScratch {
   double records[static_cast<size_t>(MP_NOALLOC_MAX_PATHS) * MP_NREC];
   WorkItem items[MP_NOALLOC_MAX_PATHS];
   DevSystem systems[MP_NOALLOC_MAX_SYSTEMS];
-  int queue[64];
+  int queue[64];  // queue[0]: the work counter, queue[1]: the kernels' error word
 };
 
 // The shared scratch.  In host code this name is a host-side stand-in, not a
@@ -62,7 +62,7 @@ extern "C" int mp_run_noalloc(const mp_system* systems, int n_systems, int preci
     if (s.lattice != MP_LATTICE_SC && s.lattice != MP_LATTICE_CHAIN) return MP_EINVAL;
     if (!(s.T > 0.0) || !std::isfinite(s.T) || !std::isfinite(s.J) || !std::isfinite(s.h))
       return MP_EINVAL;
-    if (s.n_paths < 1) return MP_EINVAL;
+    if (s.n_paths < 1 || s.path_begin < 0 || s.path_begin + s.n_paths > 0x100000000LL) return MP_EINVAL;
     if (s.lattice == MP_LATTICE_SC && (s.L < 2 || (s.L & 1) || !mpk::sweep_supports_L(precision, s.L)))
       return MP_EINVAL;
     if (s.lattice == MP_LATTICE_CHAIN && (s.L < 2 || s.L > 8192)) return MP_EINVAL;
@@ -127,6 +127,7 @@ extern "C" int mp_run_noalloc(const mp_system* systems, int n_systems, int preci
     ds.beta = 1.0 / s.T;
     ds.rec_offset = rec;
     ds.n_paths = s.n_paths;
+    ds.path_begin = s.path_begin;
     for (int64_t p = 0; p < s.n_paths; ++p) g_items[n_items++] = WorkItem{k, 1, p};
     rec += s.n_paths;
     cta = std::max(cta, tp);
@@ -144,7 +145,7 @@ extern "C" int mp_run_noalloc(const mp_system* systems, int n_systems, int preci
                       st) != cudaSuccess ||
       cudaMemcpyAsync(d->items, g_items, sizeof(WorkItem) * n_items, cudaMemcpyHostToDevice, st) !=
           cudaSuccess ||
-      cudaMemsetAsync(d->queue, 0, sizeof(int), st) != cudaSuccess) {
+      cudaMemsetAsync(d->queue, 0, 2 * sizeof(int), st) != cudaSuccess) {
     cudaGetLastError();
     return MP_ECUDA;
   }
@@ -162,6 +163,7 @@ extern "C" int mp_run_noalloc(const mp_system* systems, int n_systems, int preci
   p.s_begin = 0;
   p.s_end = n_therm + n_meas;
   p.key = mpk::philox_round_keys(seed);
+  p.error = d->queue + 1;  // where a kernel would report a path that stopped early
   mpk::ReduceParams r{};
   r.systems = d->systems;
   r.records = d->records;
