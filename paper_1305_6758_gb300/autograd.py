@@ -11,10 +11,13 @@ The forward pass is a multipath run (one system per (beta, h) pair); the backwar
 library's covariance kernel over the per-path pooled moments, weighted by the
 upstream gradients.
 
-With keep_records=False the forward pass releases its device memory and the
-backward pass recomputes the per-path records by running the same paths again:
-the random numbers are a function of (seed, system, path, sweep, site) only,
-so the recomputed records are bit-identical.
+With keep_records=False (device memory short) the forward pass runs the
+thermalisation sweeps, checkpoints every path's state to host memory
+(mp_checkpoint), runs the measurement sweeps and releases all its device
+memory.  The backward pass restores that checkpoint into a new simulation and
+recomputes only the n_meas measurement sweeps: the random numbers are a
+function of (seed, system, path, sweep, site) only, so the recomputed records,
+and the gradients, are bit-identical to those of the forward pass.
 """
 from __future__ import annotations
 
@@ -50,14 +53,23 @@ class MPObservables(torch.autograd.Function):
         if b.numel() != f.numel():
             raise ValueError("beta and h need the same length")
         sim = _simulation(b, f, spec, device)
-        sim.run()
+        keep = spec.get("keep_records", True)
+        ctx.blob = None
+        if keep:
+            sim.run()
+        else:
+            # thermalise, keep the state on the host, then measure
+            if spec["n_therm"] > 0:
+                sim.run_sweeps(spec["n_therm"])
+                ctx.blob = sim.checkpoint()
+            sim.run_sweeps(spec["n_meas"])
         ests = [sim.estimates(k) for k in range(b.numel())]
         e = torch.tensor([x["e"] for x in ests], dtype=torch.float64, device=beta.device)
         m = torch.tensor([x["m"] for x in ests], dtype=torch.float64, device=beta.device)
         ctx.spec, ctx.device, ctx.b, ctx.f = spec, device, b, f
         ctx.out_device = beta.device
         ctx.ests = ests
-        if spec.get("keep_records", True):
+        if keep:
             ctx.sim = sim
         else:
             sim.close()
@@ -67,9 +79,12 @@ class MPObservables(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g_e, g_m):
         sim = ctx.sim
-        if sim is None:  # recompute the per-path records (bit-identical)
+        if sim is None:  # replay the measurement sweeps from the checkpoint (bit-identical records)
             sim = _simulation(ctx.b, ctx.f, ctx.spec, ctx.device)
-            sim.run()
+            if ctx.blob is not None:
+                sim.restore(ctx.blob)
+            sim.run_sweeps(ctx.spec["n_meas"])
+            ctx.replay_ms = sim.timing()[0]
         n = ctx.b.numel()
         ge = torch.zeros(n, dtype=torch.float64) if g_e is None else g_e.detach()
         gm = torch.zeros(n, dtype=torch.float64) if g_m is None else g_m.detach()

@@ -106,3 +106,36 @@ def test_energy_field_derivative_against_central_difference(L, T, h0, step, term
     assert abs(f.grad.item() - fd) < 4 * se, (f.grad.item(), fd, se)
     if term_visible:
         assert abs(f.grad.item() + est["mz"] - fd) > 4 * se
+
+
+def test_backward_by_replay_from_the_thermalised_checkpoint():
+    """keep_records=False: the forward pass keeps only a host checkpoint taken
+    after thermalisation; the backward pass replays the measurement sweeps
+    from it.  Outputs and gradients equal those of keep_records=True bit for
+    bit, and the replay costs about n_meas / (n_therm + n_meas) of a full run."""
+    from paper_1305_6758_gb300.autograd import MPObservables
+
+    betas, fields = [0.62, 0.7, 0.78], [0.0, 0.01, 0.0]
+    spec = dict(L=16, n_paths=2048, n_therm=1500, n_meas=500, seed=21)
+    outs = {}
+    for keep in (True, False):
+        b = torch.tensor(betas, dtype=torch.float64, requires_grad=True)
+        f = torch.tensor(fields, dtype=torch.float64, requires_grad=True)
+        e, m = MPObservables.apply(b, f, dict(spec, keep_records=keep))
+        (e.sum() + 0.5 * m.sum()).backward()
+        outs[keep] = (e.detach().numpy(), m.detach().numpy(), b.grad.numpy(), f.grad.numpy())
+    for x, y in zip(outs[True], outs[False]):
+        np.testing.assert_array_equal(x, y)
+    # device time of the replay (n_meas sweeps) against a full run (n_therm + n_meas)
+    systems = [mp.System(16, 1 / bb, h=hh, n_paths=2048) for bb, hh in zip(betas, fields)]
+    with mp.Simulation(systems, 1500, 500, seed=21) as sim:
+        sim.run()
+        full_ms = sim.timing()[0]
+        sim.run_sweeps(1500)
+        blob = sim.checkpoint()
+    with mp.Simulation(systems, 1500, 500, seed=21) as sim:
+        sim.restore(blob)
+        sim.run_sweeps(500)
+        replay_ms = sim.timing()[0]
+    print("full run", full_ms, "ms; replay of the measurement sweeps", replay_ms, "ms")
+    assert replay_ms < 0.4 * full_ms
