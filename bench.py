@@ -20,9 +20,12 @@ unit-spin lattices drawn from Philox inside the kernels).  Workloads:
            simple cubic L=10, T=1.0, 10^4 paths, 500 + 500 sweeps, FP32.
 
 value: spin-update attempts/s over all ranks (sites x paths x sweeps /
-device time of the timed steps, max over ranks).  Each rank runs its own full
-workload (weak scaling; ranks use different seeds; no collective on the data
-path).
+device time of the timed steps, max over ranks).  Each rank runs a full
+workload's worth of paths, path ids rank x P .. (rank + 1) x P - 1 of every
+system with the same seed, so N ranks form one ensemble of N x P paths per
+system (weak scaling; no collective on the data path; rank_path_range and
+gather_records below, with mp_reduce, turn the ranks' records into that
+ensemble's estimates).
 
 --impl reference times the FP64 CPU oracle (this project's reference arm) on
 a bounded sample of the same workload on the host cores.
@@ -244,6 +247,34 @@ def max_over_ranks(x: float, dist=None, device=None) -> float:
     return t.item()
 
 
+def rank_path_range(n_paths: int, rank: int, world: int, weak: bool = True) -> tuple[int, int]:
+    """(path_begin, count) of one rank's share of a system's ensemble.
+
+    weak: every rank runs n_paths paths of its own, ids rank * n_paths onward,
+    so N ranks form one ensemble of N * n_paths paths; otherwise the n_paths
+    ids are split into contiguous blocks (the first n_paths % world ranks one
+    path more)."""
+    if weak:
+        return rank * n_paths, n_paths
+    q, r = divmod(n_paths, world)
+    begin = rank * q + min(rank, r)
+    return begin, q + (1 if rank < r else 0)
+
+
+def gather_records(rec, dist=None):
+    """Every rank's per-path records (arrays of rows), concatenated in rank
+    order on every rank; with path ranges from rank_path_range they are the
+    records of one process running all the paths."""
+    import numpy as np
+
+    rec = np.asarray(rec)
+    if dist is None:
+        return rec
+    parts = [None] * dist.get_world_size()
+    dist.all_gather_object(parts, rec)
+    return np.concatenate(parts, axis=0)
+
+
 def job_throughput(units_per_rank: float, world: int, steps: int, total_ms: float) -> float:
     """Weak scaling: every rank runs its own full workload; units/s of the whole job."""
     return units_per_rank * world * steps / (total_ms / 1e3)
@@ -278,18 +309,23 @@ def run_reference(args, w, rank):
     })
 
 
-def make_systems(mp, w, paths_override=None):
-    return [mp.System(e[0], e[1], n_paths=paths_override or e[2], lattice=lattice_of(e)) for e in w["systems"]]
+def make_systems(mp, w, paths_override=None, rank=0):
+    """The workload's systems; rank r runs path ids r x P onward of each."""
+    out = []
+    for e in w["systems"]:
+        P = paths_override or e[2]
+        out.append(mp.System(e[0], e[1], n_paths=P, lattice=lattice_of(e), path_begin=rank * P))
+    return out
 
 
-def timed_runs(mp, torch, w, dev, seed, steps, warmup, flush, barrier, gpu_id, nvtx=None):
+def timed_runs(mp, torch, w, dev, seed, steps, warmup, flush, barrier, gpu_id, nvtx=None, rank=0):
     """W untimed runs, then K runs each bracketed by CUDA events on the
     simulation's own stream (L2 flushed before each); the clocks are sampled
     during the timed runs.  Returns the simulation (open) and the timings."""
     precision = mp.FP64 if w["precision"] == "fp64" else mp.FP32
     tune = mp.FLAG_AUTOTUNE | (mp.FLAG_RANDOM_SITE if w.get("flags") == "random_site" else 0)
-    sim = mp.Simulation(make_systems(mp, w), w["n_therm"], w["n_meas"], seed=seed, precision=precision,
-                        device=dev, flags=tune)
+    sim = mp.Simulation(make_systems(mp, w, rank=rank), w["n_therm"], w["n_meas"], seed=seed,
+                        precision=precision, device=dev, flags=tune)
     for _ in range(warmup):
         sim.run()
     barrier()
@@ -461,7 +497,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    seed = 1 + rank
+    seed = 1  # one ensemble: the ranks differ in their path ids
     n_therm, n_meas = w["n_therm"], w["n_meas"]
     sweeps = n_therm + n_meas
     n_sys = len(w["systems"])
@@ -472,9 +508,10 @@ def main():
         gpu_id = "GPU-" + gpu_id
     n_sm = props.multi_processor_count
 
-    sim, t = timed_runs(mp, torch, w, dev, seed, args.steps, args.warmup, flush, barrier, gpu_id, nvtx="timed")
+    sim, t = timed_runs(mp, torch, w, dev, seed, args.steps, args.warmup, flush, barrier, gpu_id, nvtx="timed",
+                        rank=rank)
     precision, tune = t["precision"], t["tune"]
-    systems = make_systems(mp, w)
+    systems = make_systems(mp, w, rank=rank)
     total_ms = max_over_ranks(sum(t["step_ms"]), dist, dev)
     attempts_rank = attempts_of(w["systems"], sweeps)
     paths_rank = sum(e[2] for e in w["systems"])
@@ -523,7 +560,7 @@ def main():
     if args.workload == "sc16" and full_size and not args.no_sub:
         for name, (k_steps, k_warm) in SUBRECORDS.items():
             ws = WORKLOADS[name]
-            s_sim, st = timed_runs(mp, torch, ws, dev, seed, k_steps, k_warm, flush, barrier, gpu_id)
+            s_sim, st = timed_runs(mp, torch, ws, dev, seed, k_steps, k_warm, flush, barrier, gpu_id, rank=rank)
             s_plan = s_sim.plan()
             s_sim.close()
             s_ms = max_over_ranks(sum(st["step_ms"]), dist, dev)
@@ -549,7 +586,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if precision == mp.FP64 else "f32", "data": "synthetic",
             "config": {"workload": w["text"], "name": args.workload, "n_therm": n_therm, "n_meas": n_meas,
-                       "systems": n_sys, "paths": paths_rank, "parallelism": f"replicas x{world}",
+                       "systems": n_sys, "paths": paths_rank,
+                       "parallelism": f"path-id shards x{world} (one ensemble of {world} x {paths_rank} paths)",
                        "l2": "flushed between timed steps (256 MB write)", "plan": plan_main,
                        "autotuned": autotuned},
             "paths_per_s": paths_per_s,

@@ -50,7 +50,9 @@ extern "C" {
 #define MP_ECUDA (-3)      /* a CUDA runtime call failed; see mp_last_error */
 #define MP_ESTATE (-4)     /* call out of order, e.g. estimates before a run */
 #define MP_ECANCELED (-5)  /* mp_cancel stopped the run before it finished */
-#define MP_ETIMEOUT (-6)   /* reserved: the library has no unbounded waits */
+#define MP_ETIMEOUT (-6)   /* a bounded wait in a kernel gave up (a bulk copy of
+                              the streamed path did not arrive within ~2 s); the
+                              run's results are invalid, the context stays usable */
 
 /* ---------------------------------------------------------------- enums --- */
 #define MP_LATTICE_SC 0    /* periodic simple cubic, N = L^3, L even */
@@ -149,7 +151,10 @@ enum {
  *   cv_m     = se(<|m|>) / <|m|>                             Eq. (eq:cv)
  *   r_*      = 1 - ||R||^2 / ((P-1) sigma^2) of the normal Q-Q line fit of the
  *              per-path values, plotting positions (i - 1/2)/P,
- *              Eq. (dist-coefficient); NaN when P < 3 or P > MP_R_MAX_PATHS.
+ *              Eq. (dist-coefficient); NaN when P < 3.  Up to MP_R_MAX_PATHS
+ *              paths the values are sorted in shared memory; a handle with a
+ *              larger system sorts in a device buffer of 2 P doubles per
+ *              system, allocated at create.
  * SEs of derived quantities are delete-one jackknife over paths. */
 #define MP_R_MAX_PATHS 16384
 
@@ -172,7 +177,12 @@ typedef struct {
    * the ordered state (Sec. 4).  start_z = max over X in {e, |m|} of
    * |X_a - X_b| / sqrt(X_a_se^2 + X_b_se^2), skipping an undefined 0/0. */
   double e_a, e_a_se, e_b, e_b_se, m_a, m_a_se, m_b, m_b_se, start_z;
-  double reserved[2];
+  /* Device time of the run these estimates come from, in seconds: the sweep
+   * kernel and the reduction kernel, from CUDA events on the handle's stream
+   * (filled in by mp_estimates; NaN from mp_run_noalloc, which records no
+   * events). */
+  double elapsed_s;
+  double reserved[1];
 } mp_estimates_t; /* 64 doubles */
 
 #define MP_NEST 64
@@ -185,6 +195,12 @@ typedef struct {
   double J;        /* exchange; J > 0 ferro, J < 0 antiferro (Sec. 2.1) */
   double h;        /* field along +z (not in the paper; 0 reproduces it) */
   int64_t n_paths; /* independent paths of this system, >= 1 */
+  int64_t path_begin; /* path id of the first path: path k of the system draws
+                         the random numbers of path id path_begin + k, so
+                         processes that split one ensemble run disjoint ranges
+                         with the same seed; 0 for a whole ensemble.
+                         path_begin + n_paths <= 2^32.  MP_FLAG_TWO_START
+                         halves the local range 0 .. n_paths-1 */
 } mp_system;
 
 /* Device-memory allocator hooks.  alloc must return device memory of at least
@@ -342,6 +358,24 @@ int mp_cancel(mp_handle h);
  * Errors: MP_EINVAL (bad index). */
 int mp_system_plan(mp_handle h, int system, int* threads_per_path, int* paths_per_cta,
                    int* streamed_from_hbm);
+
+/* Ensemble estimates of per-path records the caller holds: the reduction
+ * kernel of mp_run (Sec. 2.2: Eq. MCAV, Eq. cv, Eq. kum, Eq. eq:cv and the
+ * distribution coefficient of Sec. 3) on d_records, MP_NREC doubles per path,
+ * the systems' paths one after another in `systems` order (device memory,
+ * caller-owned, read only), written to d_estimates, MP_NEST doubles per
+ * system (device memory, caller-owned; elapsed_s is NaN).  n_therm and n_meas
+ * are the schedule the records come from (they enter n_meas and attempts).
+ * For processes that each ran part of one ensemble (disjoint path_begin
+ * ranges of the same systems and seed): gather their records in path order
+ * and reduce them here to obtain exactly the estimates of one process
+ * running every path.  Allocates and frees a small device table (and, for
+ * systems of more than MP_R_MAX_PATHS paths, 2 x paths doubles of sort
+ * space) and synchronises `stream` (cudaStream_t; NULL = legacy default).
+ * Errors: MP_EINVAL (NULL pointer, bad system), MP_ENOMEM, MP_ECUDA; the text
+ * is mp_last_error(NULL). */
+int mp_reduce(const mp_system* systems, int n_systems, int64_t n_therm, int64_t n_meas,
+              const double* d_records, double* d_estimates, void* stream);
 
 /* Philox4x32-10 of n counters: d_ctr holds 4n uint32 words (c0 c1 c2 c3 per
  * counter), d_out receives 4n words.  Device pointers, caller-owned; queued

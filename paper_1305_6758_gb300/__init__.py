@@ -54,7 +54,8 @@ _STATUS = {0: "MP_OK", -1: "MP_EINVAL", -2: "MP_ENOMEM", -3: "MP_ECUDA", -4: "MP
 
 class MPSystem(ctypes.Structure):
     _fields_ = [("lattice", ctypes.c_int32), ("L", ctypes.c_int32), ("T", ctypes.c_double),
-                ("J", ctypes.c_double), ("h", ctypes.c_double), ("n_paths", ctypes.c_int64)]
+                ("J", ctypes.c_double), ("h", ctypes.c_double), ("n_paths", ctypes.c_int64),
+                ("path_begin", ctypes.c_int64)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t)
@@ -87,11 +88,12 @@ EST_FIELDS = [
     "r_e", "r_m", "r_mx", "r_my", "r_mz", "r_amz",
     "attempts", "norm_max",
     "e_a", "e_a_se", "e_b", "e_b_se", "m_a", "m_a_se", "m_b", "m_b_se", "start_z",
+    "elapsed_s",
 ]
 
 
 class MPEstimates(ctypes.Structure):
-    _fields_ = [(f, ctypes.c_double) for f in EST_FIELDS] + [("reserved", ctypes.c_double * 2)]
+    _fields_ = [(f, ctypes.c_double) for f in EST_FIELDS] + [("reserved", ctypes.c_double * 1)]
 
 
 assert ctypes.sizeof(MPEstimates) == NEST * 8
@@ -101,7 +103,7 @@ EXPORTS = [
     "mp_create", "mp_create_ex", "mp_run", "mp_set_seed", "mp_estimates", "mp_paths",
     "mp_device_buffers", "mp_spins", "mp_backward", "mp_timing", "mp_plan", "mp_system_plan",
     "mp_run_sweeps", "mp_progress", "mp_checkpoint", "mp_restore", "mp_cancel", "mp_philox",
-    "mp_destroy", "mp_last_error", "mp_status_string",
+    "mp_reduce", "mp_destroy", "mp_last_error", "mp_status_string",
 ]
 
 _lib = None
@@ -138,6 +140,8 @@ def load_library(path: str = LIB_PATH):
     lib.mp_restore.argtypes = [H, ctypes.c_void_p, ctypes.c_size_t]
     lib.mp_cancel.argtypes = [H]
     lib.mp_philox.argtypes = [ctypes.c_void_p, i64, u64, ctypes.c_void_p, ctypes.c_void_p]
+    lib.mp_reduce.argtypes = [P(MPSystem), ctypes.c_int, i64, i64, ctypes.c_void_p, ctypes.c_void_p,
+                              ctypes.c_void_p]
     for name in EXPORTS:
         getattr(lib, name).restype = ctypes.c_int
     lib.mp_destroy.argtypes = [H]
@@ -182,7 +186,12 @@ class _TorchAllocator:
 
 @dataclass
 class System:
-    """One system of a batch: lattice kind, size, temperature, couplings, paths."""
+    """One system of a batch: lattice kind, size, temperature, couplings, paths.
+
+    ``path_begin`` is the path id of the first path: a process that runs part
+    of one ensemble (paths path_begin .. path_begin + n_paths - 1, same seed)
+    draws exactly those paths' random numbers.
+    """
 
     L: int
     T: float
@@ -190,6 +199,7 @@ class System:
     h: float = 0.0
     n_paths: int = 1
     lattice: int = SC
+    path_begin: int = 0
 
     @property
     def N(self) -> int:
@@ -217,7 +227,7 @@ class Simulation:
         self.device = torch.device(device if device is not None else "cuda:0")
         self.systems = list(systems)
         self._sys = (MPSystem * len(systems))(
-            *[MPSystem(s.lattice, s.L, s.T, s.J, s.h, s.n_paths) for s in systems])
+            *[MPSystem(s.lattice, s.L, s.T, s.J, s.h, s.n_paths, s.path_begin) for s in systems])
         self._alloc = _TorchAllocator(self.device)
         # a stream of its own (PyTorch's default stream is the legacy NULL stream)
         self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
@@ -390,6 +400,25 @@ def philox(counters: np.ndarray, seed: int, device="cuda:0") -> np.ndarray:
     _check(lib.mp_philox(c.data_ptr(), c.shape[0], seed, out.data_ptr(), st.cuda_stream))
     st.synchronize()
     return out.cpu().numpy().view(np.uint32)
+
+
+def reduce_records(systems: list[System], n_therm: int, n_meas: int, records, device="cuda:0") -> list[dict]:
+    """Estimates of per-path records (a float64 CUDA tensor of n_paths x NREC
+    rows, systems one after another) through mp_reduce: for ranks that each
+    ran part of one ensemble and gathered their records in path order."""
+    import torch
+
+    lib = load_library()
+    rec = records.to(device=device, dtype=torch.float64).contiguous()
+    n = len(systems)
+    if rec.numel() != sum(s.n_paths for s in systems) * NREC:
+        raise ValueError("records do not match the systems' path counts")
+    arr = (MPSystem * n)(*[MPSystem(s.lattice, s.L, s.T, s.J, s.h, s.n_paths, s.path_begin) for s in systems])
+    out = torch.empty(n * NEST, dtype=torch.float64, device=rec.device)
+    st = torch.cuda.current_stream(rec.device)
+    _check(lib.mp_reduce(arr, n, n_therm, n_meas, rec.data_ptr(), out.data_ptr(), st.cuda_stream))
+    est = out.cpu().numpy().reshape(n, NEST)
+    return [dict(zip(EST_FIELDS, row)) for row in est]
 
 
 def simulate(L: int, T: float, J: float = 1.0, h: float = 0.0, n_paths: int = 256,

@@ -41,6 +41,7 @@ struct DevSystem {
   int64_t n_paths;
   int32_t mode;         // kModeShared / kModeStreamed / kModePair / kModeGlobal
   int32_t pad;
+  int64_t path_begin;   // path id (random-number counter) of the system's path 0
 };
 
 constexpr int kModeShared = 0;

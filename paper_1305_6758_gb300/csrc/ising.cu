@@ -96,7 +96,7 @@ __device__ void run_path_ising(const DevSystem& sy, int sys_idx, int64_t path,
   unsigned char* base = slice + slice_spin_offset(tp, sy.ring);
   unsigned long long* thr = reinterpret_cast<unsigned long long*>(base);
   int8_t* sp = reinterpret_cast<int8_t*>(base + kThrBytes);
-  const uint32_t c2 = static_cast<uint32_t>(path);
+  const uint32_t c2 = static_cast<uint32_t>(sy.path_begin + path);  // path id
   const uint32_t sys_hi = static_cast<uint32_t>(sys_idx) << 8;
   const int init = path_init_mode(P.init_mode, path, sy.n_paths);
   const int64_t j_first = P.s_begin > P.n_therm ? P.s_begin - P.n_therm : 0;

@@ -14,6 +14,10 @@ struct ReduceParams {
   const double* records;
   double* est;  // MP_NEST doubles per system
   int64_t n_therm, n_meas;
+  // Sort space for the distribution coefficient of systems with more than
+  // MP_R_MAX_PATHS paths: 2 n_paths doubles at 2 rec_offset per system
+  // (nullptr when no system is that large).
+  double* sort_buf;
 };
 
 struct BackwardParams {

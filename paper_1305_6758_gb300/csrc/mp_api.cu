@@ -165,6 +165,7 @@ struct mp_state {
   double* d_spins = nullptr;
   int64_t* d_spin_offset = nullptr;
   unsigned long long* d_thr = nullptr;  // Ising acceptance thresholds, 10 per system
+  double* d_sort = nullptr;        // sort space of the distribution coefficient (systems > 16384 paths)
   int* d_error = nullptr;          // nonzero when a bounded wait in a kernel gave up
   void* d_lattice = nullptr;       // HBM lattices of streamed paths
   size_t lattice_capacity = 0;     // bytes allocated at d_lattice
@@ -263,6 +264,37 @@ void release(mp_state* h) {
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
+// Every system of a batch: lattice kind, size, temperature, couplings, paths.
+int validate_systems(const mp_system* systems, int n, uint32_t flags) {
+  for (int k = 0; k < n; ++k) {
+    const mp_system& s = systems[k];
+    if (s.lattice != MP_LATTICE_SC && s.lattice != MP_LATTICE_CHAIN && s.lattice != MP_LATTICE_ISING)
+      return fail(nullptr, MP_EINVAL, "system %d: unknown lattice %d", k, s.lattice);
+    if ((s.lattice == MP_LATTICE_ISING) != (systems[0].lattice == MP_LATTICE_ISING))
+      return fail(nullptr, MP_EINVAL, "Ising and Heisenberg systems cannot share a batch");
+    if (s.lattice == MP_LATTICE_ISING && (flags & MP_FLAG_RANDOM_SITE))
+      return fail(nullptr, MP_EINVAL, "the random-site order is built for Heisenberg systems only");
+    if (!(s.T > 0.0) || !std::isfinite(s.T) || !std::isfinite(s.J) || !std::isfinite(s.h))
+      return fail(nullptr, MP_EINVAL, "system %d: need finite T > 0, J, h", k);
+    if (s.n_paths < 1 || s.n_paths > 0x7fffffffLL)
+      return fail(nullptr, MP_EINVAL, "system %d: n_paths must be in 1..2^31-1", k);
+    if (s.path_begin < 0 || s.path_begin + s.n_paths > 0x100000000LL)
+      return fail(nullptr, MP_EINVAL, "system %d: path ids path_begin .. path_begin + n_paths - 1 "
+                  "must lie in 0..2^32-1", k);
+    if (s.lattice == MP_LATTICE_SC) {
+      if (s.L < 2 || (s.L & 1))
+        return fail(nullptr, MP_EINVAL, "system %d: simple cubic L must be even and >= 2", k);
+      if (s.L > 1024) return fail(nullptr, MP_EINVAL, "system %d: L=%d above 1024", k, s.L);
+    } else if (s.lattice == MP_LATTICE_ISING) {
+      if (s.L < 2 || (s.L & 1) || s.L > MP_ISING_MAX_L)
+        return fail(nullptr, MP_EINVAL, "system %d: Ising L must be even in 2..%d", k, MP_ISING_MAX_L);
+    } else if (s.L < 2 || s.L > 8192) {
+      return fail(nullptr, MP_EINVAL, "system %d: chain length must be in 2..8192", k);
+    }
+  }
+  return MP_OK;
+}
+
 int validate(const mp_config* cfg) {
   if (!cfg) return fail(nullptr, MP_EINVAL, "config is NULL");
   if (cfg->precision != MP_FP32 && cfg->precision != MP_FP64)
@@ -282,30 +314,7 @@ int validate(const mp_config* cfg) {
   if (cfg->threads_per_path != 0 &&
       (cfg->threads_per_path < 32 || cfg->threads_per_path > kMaxCta || cfg->threads_per_path % 32))
     return fail(nullptr, MP_EINVAL, "threads_per_path must be a multiple of 32 in 32..1024");
-  for (int k = 0; k < cfg->n_systems; ++k) {
-    const mp_system& s = cfg->systems[k];
-    if (s.lattice != MP_LATTICE_SC && s.lattice != MP_LATTICE_CHAIN && s.lattice != MP_LATTICE_ISING)
-      return fail(nullptr, MP_EINVAL, "system %d: unknown lattice %d", k, s.lattice);
-    if ((s.lattice == MP_LATTICE_ISING) != (cfg->systems[0].lattice == MP_LATTICE_ISING))
-      return fail(nullptr, MP_EINVAL, "Ising and Heisenberg systems cannot share a batch");
-    if (s.lattice == MP_LATTICE_ISING && (cfg->flags & MP_FLAG_RANDOM_SITE))
-      return fail(nullptr, MP_EINVAL, "the random-site order is built for Heisenberg systems only");
-    if (!(s.T > 0.0) || !std::isfinite(s.T) || !std::isfinite(s.J) || !std::isfinite(s.h))
-      return fail(nullptr, MP_EINVAL, "system %d: need finite T > 0, J, h", k);
-    if (s.n_paths < 1 || s.n_paths > 0x7fffffffLL)
-      return fail(nullptr, MP_EINVAL, "system %d: n_paths must be in 1..2^31-1", k);
-    if (s.lattice == MP_LATTICE_SC) {
-      if (s.L < 2 || (s.L & 1))
-        return fail(nullptr, MP_EINVAL, "system %d: simple cubic L must be even and >= 2", k);
-      if (s.L > 1024) return fail(nullptr, MP_EINVAL, "system %d: L=%d above 1024", k, s.L);
-    } else if (s.lattice == MP_LATTICE_ISING) {
-      if (s.L < 2 || (s.L & 1) || s.L > MP_ISING_MAX_L)
-        return fail(nullptr, MP_EINVAL, "system %d: Ising L must be even in 2..%d", k, MP_ISING_MAX_L);
-    } else if (s.L < 2 || s.L > 8192) {
-      return fail(nullptr, MP_EINVAL, "system %d: chain length must be in 2..8192", k);
-    }
-  }
-  return MP_OK;
+  return validate_systems(cfg->systems, cfg->n_systems, cfg->flags);
 }
 
 // Launch shape: threads per path from the sites per colour (about 8 sites per
@@ -506,6 +515,7 @@ int plan(mp_state* h, const mp_config* cfg) {
     d.beta = 1.0 / s.T;
     d.rec_offset = rec;
     d.n_paths = s.n_paths;
+    d.path_begin = s.path_begin;
     d.mode = paired(s, h->precision, h->flags) ? kModePair
              : global(s)                         ? kModeGlobal
              : streamed(s, h->precision, h->flags) ? kModeStreamed : kModeShared;
@@ -582,6 +592,7 @@ int plan_random_site(mp_state* h) {
     d.beta = 1.0 / s.T;
     d.rec_offset = rec;
     d.n_paths = s.n_paths;
+    d.path_begin = s.path_begin;
     d.mode = kModeShared;
     rec += s.n_paths;
     h->spin_offset[k] = spins;
@@ -639,6 +650,7 @@ int enqueue_run(mp_state* h, int64_t s_begin, int64_t s_end, bool resume, bool s
   r.est = h->d_est;
   r.n_therm = std::min(s_end, h->n_therm);
   r.n_meas = std::max<int64_t>(0, s_end - h->n_therm);
+  r.sort_buf = h->d_sort;
   const unsigned evflag = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   MP_CUDA(h, cudaMemsetAsync(h->d_queue, 0, 2 * sizeof(int), h->stream));
   MP_CUDA(h, cudaMemsetAsync(h->d_error, 0, sizeof(int), h->stream));
@@ -935,6 +947,10 @@ int mp_create_ex(const mp_config* cfg, mp_handle* out) {
     return bail(fail(h, MP_ENOMEM, "device allocation failed"));
   h->d_error = static_cast<int*>(dev_alloc(h, 256));
   if (!h->d_error) return bail(fail(h, MP_ENOMEM, "device allocation failed"));
+  if (h->max_paths > MP_R_MAX_PATHS) {  // sorting space for r beyond shared memory
+    h->d_sort = static_cast<double*>(dev_alloc(h, sizeof(double) * 2 * h->total_paths));
+    if (!h->d_sort) return bail(fail(h, MP_ENOMEM, "sort buffer allocation failed"));
+  }
   if (h->flags & MP_FLAG_KEEP_SPINS) {
     h->d_spins = static_cast<double*>(dev_alloc(h, sizeof(double) * h->total_spins));
     if (!h->d_spins) return bail(fail(h, MP_ENOMEM, "spin buffer allocation failed"));
@@ -1004,6 +1020,9 @@ int mp_estimates(mp_handle h, int system, mp_estimates_t* out) {
   MP_CUDA(h, cudaMemcpyAsync(out, h->d_est + static_cast<int64_t>(system) * MP_NEST,
                              sizeof(mp_estimates_t), cudaMemcpyDeviceToHost, h->stream));
   MP_CUDA(h, cudaStreamSynchronize(h->stream));
+  float ms = 0.f;  // sweep and reduction kernels of the last run
+  out->elapsed_s = cudaEventElapsedTime(&ms, h->ev[0], h->ev[2]) == cudaSuccess ? 1e-3 * ms : NAN;
+  cudaGetLastError();
   return check_error_flag(h);
 }
 
@@ -1143,6 +1162,7 @@ uint64_t config_hash(const mp_state* h) {
     mix(&s.J, sizeof(s.J));
     mix(&s.h, sizeof(s.h));
     mix(&s.n_paths, sizeof(s.n_paths));
+    mix(&s.path_begin, sizeof(s.path_begin));
   }
   for (const DevSystem& d : h->hsys) mix(&d.mode, sizeof(d.mode));
   mix(&h->precision, sizeof(h->precision));
@@ -1249,6 +1269,63 @@ int mp_system_plan(mp_handle h, int system, int* threads_per_path, int* paths_pe
   // 0 shared memory, 1 streamed from HBM, 2 two-CTA cluster, 3 in place in HBM
   if (streamed_from_hbm) *streamed_from_hbm = d.mode;
   return MP_OK;
+}
+
+int mp_reduce(const mp_system* systems, int n_systems, int64_t n_therm, int64_t n_meas,
+              const double* d_records, double* d_estimates, void* stream) {
+  g_create_error.clear();
+  if (!systems || !d_records || !d_estimates || n_systems < 1 || n_systems > 65535)
+    return fail(nullptr, MP_EINVAL, "NULL pointer or n_systems outside 1..65535");
+  if (n_therm < 0 || n_meas < 0) return fail(nullptr, MP_EINVAL, "negative sweep counts");
+  int rc = validate_systems(systems, n_systems, 0);
+  if (rc != MP_OK) return rc;
+  std::vector<DevSystem> table(n_systems);
+  int64_t rec = 0, max_paths = 0;
+  for (int k = 0; k < n_systems; ++k) {
+    const mp_system& s = systems[k];
+    DevSystem& d = table[k];
+    d = DevSystem{};
+    d.lattice = s.lattice;
+    d.L = s.L;
+    d.N = static_cast<int32_t>(sites_of(s));
+    d.NH = (d.N + 1) / 2;
+    d.T = s.T;
+    d.J = s.J;
+    d.h = s.h;
+    d.beta = 1.0 / s.T;
+    d.rec_offset = rec;
+    d.n_paths = s.n_paths;
+    d.path_begin = s.path_begin;
+    rec += s.n_paths;
+    max_paths = std::max(max_paths, s.n_paths);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  DevSystem* d_sys = nullptr;
+  double* d_sort = nullptr;
+  auto done = [&](int code) {
+    if (d_sys) cudaFree(d_sys);
+    if (d_sort) cudaFree(d_sort);
+    cudaGetLastError();
+    return code;
+  };
+  if (cudaMalloc(&d_sys, sizeof(DevSystem) * n_systems) != cudaSuccess ||
+      (max_paths > MP_R_MAX_PATHS && cudaMalloc(&d_sort, sizeof(double) * 2 * rec) != cudaSuccess))
+    return done(fail(nullptr, MP_ENOMEM, "device allocation failed"));
+  cudaError_t e = reduce_prepare();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_sys, table.data(), sizeof(DevSystem) * n_systems, cudaMemcpyHostToDevice, st);
+  ReduceParams r{};
+  r.systems = d_sys;
+  r.records = d_records;
+  r.est = d_estimates;
+  r.n_therm = n_therm;
+  r.n_meas = n_meas;
+  r.sort_buf = d_sort;
+  if (e == cudaSuccess) e = launch_reduce(r, n_systems, max_paths, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess)
+    return done(fail(nullptr, MP_ECUDA, "mp_reduce: %s", cudaGetErrorString(e)));
+  return done(MP_OK);
 }
 
 int mp_philox(const uint32_t* d_ctr, int64_t n, uint64_t seed, uint32_t* d_out, void* stream) {

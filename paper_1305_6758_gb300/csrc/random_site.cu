@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(128) random_site_kernel(const SweepParams P, i
     S.plane = plane;
   }
   auto el = [&](int i) { return base + static_cast<int64_t>(i) * Pk; };
-  const uint32_t c2 = static_cast<uint32_t>(path);
+  const uint32_t c2 = static_cast<uint32_t>(sy.path_begin + path);  // path id
   const uint32_t sys_hi = static_cast<uint32_t>(k) << 8;
   const int init = path_init_mode(P.init_mode, path, Pk);
   for (int i = 0; i < N; ++i) {

@@ -79,8 +79,10 @@ __device__ void derived(const double* mu, double N, double beta, double* th) {
 }
 
 // Eq. (dist-coefficient) of one record field: sort the P values (bitonic, in
-// shared memory), fit them to the normal quantiles at (i - 1/2)/P by least
-// squares; r = 1 - SS_res / ((P-1) sigma^2) = S_xq^2 / (S_xx S_qq).
+// `keys`: shared memory up to MP_R_MAX_PATHS paths, a device buffer of at
+// least the next power of two above P beyond), fit them to the normal
+// quantiles at (i - 1/2)/P by least squares;
+// r = 1 - SS_res / ((P-1) sigma^2) = S_xq^2 / (S_xx S_qq).
 __device__ double distribution_coefficient(const double* rec, int64_t P, int field, double mean,
                                            double* keys, double* scratch) {
   int n = 1;
@@ -234,10 +236,13 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const ReduceParams 
 
   // pass 5: distribution coefficients of the per-path outputs
   const int rfield[6] = {MP_R_E, MP_R_M, MP_R_MX, MP_R_MY, MP_R_MZ, MP_R_AMZ};
+  double* sort_keys = P <= MP_R_MAX_PATHS ? keys
+                      : (p.sort_buf != nullptr && P <= (int64_t{1} << 30)) ? p.sort_buf + 2 * sy.rec_offset
+                                                                           : nullptr;
   double rcoef[6];
   for (int f = 0; f < 6; ++f) {
-    rcoef[f] = (P >= 3 && P <= MP_R_MAX_PATHS)
-                   ? distribution_coefficient(rec, P, rfield[f], mu[rfield[f]], keys, scratch)
+    rcoef[f] = (P >= 3 && sort_keys != nullptr)
+                   ? distribution_coefficient(rec, P, rfield[f], mu[rfield[f]], sort_keys, scratch)
                    : NAN;
   }
 
@@ -290,7 +295,8 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const ReduceParams 
     const double ze = fabs(o->e_a - o->e_b) / sqrt(o->e_a_se * o->e_a_se + o->e_b_se * o->e_b_se);
     const double zm = fabs(o->m_a - o->m_b) / sqrt(o->m_a_se * o->m_a_se + o->m_b_se * o->m_b_se);
     o->start_z = fmax(ze, zm);  // an undefined ratio (0/0) is skipped
-    for (int k = 0; k < 2; ++k) o->reserved[k] = 0.0;
+    o->elapsed_s = NAN;  // the host fills it in from the run's events
+    o->reserved[0] = 0.0;
   }
 }
 

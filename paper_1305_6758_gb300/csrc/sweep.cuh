@@ -634,7 +634,7 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
   using A = Arith<Real>;
   Real* sp = hbm_spins ? hbm_spins : reinterpret_cast<Real*>(slice + slice_spin_offset(tp, sy.ring));
   const int S = geo.stride();
-  const uint32_t c2 = static_cast<uint32_t>(path);
+  const uint32_t c2 = static_cast<uint32_t>(sy.path_begin + path);  // path id
   const uint32_t c3u = kTagUpdate | (static_cast<uint32_t>(sys_idx) << 8);
   const uint32_t c3i = kTagInit | (static_cast<uint32_t>(sys_idx) << 8);
   const int init = path_init_mode(P.init_mode, path, sy.n_paths);
@@ -879,7 +879,7 @@ __device__ void run_path_pair(const DevSystem& sy, int sys_idx, int64_t path, co
   Real* sp = reinterpret_cast<Real*>(slice + slice_spin_offset(2 * tp, sy.ring));
   Real* partner_sp = map_rank(sp, rank ^ 1u);
   const int zbase = static_cast<int>(rank) * ZL;
-  const uint32_t c2 = static_cast<uint32_t>(path);
+  const uint32_t c2 = static_cast<uint32_t>(sy.path_begin + path);  // path id
   const uint32_t c3u = kTagUpdate | (static_cast<uint32_t>(sys_idx) << 8);
   const uint32_t c3i = kTagInit | (static_cast<uint32_t>(sys_idx) << 8);
   const int init = path_init_mode(P.init_mode, path, sy.n_paths);
@@ -1166,7 +1166,7 @@ __device__ void run_path_streamed(const DevSystem& sy, int sys_idx, int64_t path
   Real* lat = st ? reinterpret_cast<Real*>(st + kStateHeader) : lat_cta;
   auto plane = [&](int z, int c) { return lat + (static_cast<int64_t>(z) * 2 + c) * hps; };
   auto wrap = [&](int q) { return ((q % L) + L) % L; };
-  const uint32_t c2 = static_cast<uint32_t>(path);
+  const uint32_t c2 = static_cast<uint32_t>(sy.path_begin + path);  // path id
   const uint32_t c3u = kTagUpdate | (static_cast<uint32_t>(sys_idx) << 8);
   const uint32_t c3i = kTagInit | (static_cast<uint32_t>(sys_idx) << 8);
   const int init = path_init_mode(P.init_mode, path, sy.n_paths);

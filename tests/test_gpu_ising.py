@@ -95,18 +95,21 @@ def test_ising_onsager_yang_paper_sizes():
 
 
 def test_ising_binder_crossing():
-    """Appendix A: U_L of L = 50 and 60 cross near T_C = 2.269(10)."""
+    """Appendix A: U_L of L = 50 and 60 cross inside the paper's T_C = 2.269(10):
+    the larger lattice's U_L is above the smaller one's by 3 standard errors
+    below T_C and below it by 3 above T_C, and the interpolated crossing lies
+    within the printed error."""
     l_small, l_large, tc_paper, tc_err = golden.critical_temperature("ising_square")
     Ts = [2.24, 2.26, 2.28, 2.30]
-    systems = [mp.System(L, T, n_paths=4096, lattice=mp.ISING) for L in (l_small, l_large) for T in Ts]
+    systems = [mp.System(L, T, n_paths=8192, lattice=mp.ISING) for L in (l_small, l_large) for T in Ts]
     _, ests, _ = run(systems, 20000, 10000, seed=9)  # the appendix's 3 x 10^4 sweeps
     u50 = np.array([e["binder"] for e in ests[:4]])
     u60 = np.array([e["binder"] for e in ests[4:]])
     se = np.hypot([e["binder_se"] for e in ests[:4]], [e["binder_se"] for e in ests[4:]])
     d = u60 - u50
     print("U50", u50, "U60", u60, "d/se", d / se)
-    assert d[0] > 2 * se[0] and d[-1] < -2 * se[-1]
+    assert d[0] > 3 * se[0] and d[-1] < -3 * se[-1]
     k = int(np.nonzero((d[:-1] > 0) & (d[1:] <= 0))[0][0])
     tc = Ts[k] + (Ts[k + 1] - Ts[k]) * d[k] / (d[k] - d[k + 1])
     print("crossing", tc)
-    assert abs(tc - tc_paper) < 2 * tc_err
+    assert abs(tc - tc_paper) < tc_err

@@ -215,6 +215,25 @@ def test_field_derivatives_reduction_and_backward():
     assert abs(ests[1]["de_dh"] - closed) < 4 * ests[1]["de_dh_se"], (ests[1]["de_dh"], closed)
 
 
+def test_distribution_coefficient_beyond_shared_memory_sort():
+    """Eq. (dist-coefficient) for systems of more than 16384 paths (sorted in a
+    device buffer instead of shared memory) equals the oracle's r of the same
+    records; a small system of the same batch keeps the shared-memory sort; the
+    estimates carry the run's device time."""
+    systems = [mp.System(4, 1.5, n_paths=20000), mp.System(4, 0.9, n_paths=700)]
+    with mp.Simulation(systems, 10, 20, seed=13, precision=mp.FP64) as sim:
+        sim.run()
+        recs = [sim.paths(k) for k in range(2)]
+        ests = [sim.estimates(k) for k in range(2)]
+        sweep_ms, reduce_ms = sim.timing()
+    for k, s in enumerate(systems):
+        oest = O.estimates(recs[k], 64, s.T)
+        for key in ("r_e", "r_m", "r_mx", "r_my", "r_mz", "r_amz"):
+            assert np.isfinite(ests[k][key])
+            assert ests[k][key] == pytest.approx(oest[key], rel=1e-9, abs=1e-12), (k, key)
+        assert ests[k]["elapsed_s"] == pytest.approx((sweep_ms + reduce_ms) / 1e3, rel=1e-3)
+
+
 # ---------------------------------------------------------------- errors ---
 def test_status_codes():
     with pytest.raises(mp.MPError) as ei:
