@@ -44,13 +44,21 @@ cudaError_t launch_sweep(int precision, int variant, const SweepParams& p, int g
 constexpr int kStreamL32 = -1032;
 constexpr int kStreamL64 = -1064;
 
-// The square-lattice Ising kernel (variant kIsingKernel), any even L.
+// The square-lattice Ising kernels: variant kIsingKernel runs any even L;
+// ising_variant(L) a batch whose systems all have the size L, compiled for it
+// (L in 20, 40, 50, 60: ising_compiled_L).
 constexpr int kIsingKernel = -3;
-cudaError_t ising_prepare(int device, int* max_dynamic, int* max_threads);
-cudaError_t ising_occupancy(int cta, int smem, int* blocks);
-cudaError_t launch_ising(const SweepParams& p, int grid, int cta, int smem, cudaStream_t st);
-// Slice bytes of an Ising path: thresholds (128 bytes) then one byte per spin.
+constexpr int ising_variant(int L) { return -3000 - L; }
+constexpr int ising_variant_L(int v) { return v <= -3000 ? -3000 - v : 0; }
+constexpr bool is_ising_variant(int v) { return v == kIsingKernel || v <= -3000; }
+bool ising_compiled_L(int L);
+cudaError_t ising_prepare(int variant, int device, int* max_dynamic, int* max_threads);
+cudaError_t ising_occupancy(int variant, int cta, int smem, int* blocks);
+cudaError_t launch_ising(int variant, const SweepParams& p, int grid, int cta, int smem, cudaStream_t st);
+// Slice bytes of an Ising path: thresholds (128 bytes), then per colour L + 2
+// rows of L/2 bytes (the lattice's rows and a copy of each boundary row).
 constexpr int kIsingThrBytes = 128;
+constexpr int ising_slice_spin_bytes(int L) { return kIsingThrBytes + 2 * (L / 2) * (L + 2); }
 
 // The random-site order (MP_FLAG_RANDOM_SITE, variant kRandomSiteKernel): one
 // thread per path, lattices in HBM (random_site_bytes_per_site bytes per site

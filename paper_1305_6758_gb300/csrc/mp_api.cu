@@ -40,12 +40,12 @@ bool sweep_supports_L(int precision, int L) {
 }
 cudaError_t sweep_prepare(int precision, int variant, int device, int* max_dynamic,
                           int* max_threads) {
-  if (variant == kIsingKernel) return ising_prepare(device, max_dynamic, max_threads);
+  if (is_ising_variant(variant)) return ising_prepare(variant, device, max_dynamic, max_threads);
   return precision == MP_FP64 ? sweep_prepare_fp64(variant, device, max_dynamic, max_threads)
                               : sweep_prepare_fp32(variant, device, max_dynamic, max_threads);
 }
 cudaError_t sweep_occupancy(int precision, int variant, int cta, int smem, int* blocks) {
-  if (variant == kIsingKernel) return ising_occupancy(cta, smem, blocks);
+  if (is_ising_variant(variant)) return ising_occupancy(variant, cta, smem, blocks);
   return precision == MP_FP64 ? sweep_occupancy_fp64(variant, cta, smem, blocks)
                               : sweep_occupancy_fp32(variant, cta, smem, blocks);
 }
@@ -55,7 +55,7 @@ cudaError_t sweep_cluster_occupancy(int precision, int variant, int cta, int sme
 }
 cudaError_t launch_sweep(int precision, int variant, const SweepParams& p, int grid, int cta,
                          int smem, cudaStream_t st) {
-  if (variant == kIsingKernel) return launch_ising(p, grid, cta, smem, st);
+  if (is_ising_variant(variant)) return launch_ising(variant, p, grid, cta, smem, st);
   return precision == MP_FP64 ? launch_sweep_fp64(variant, p, grid, cta, smem, st)
                               : launch_sweep_fp32(variant, p, grid, cta, smem, st);
 }
@@ -337,7 +337,7 @@ int plan(mp_state* h, const mp_config* cfg) {
   auto global = [&](const mp_system& sy) { return in_place(sy, h->precision, h->flags, optin); };
   // lattices held by two-CTA clusters run in the mixed-size kernel
   auto variant_of = [&](const mp_system& sy) {
-    if (sy.lattice == MP_LATTICE_ISING) return kIsingKernel;
+    if (sy.lattice == MP_LATTICE_ISING) return ising_compiled_L(sy.L) ? ising_variant(sy.L) : kIsingKernel;
     if (sy.lattice == MP_LATTICE_CHAIN) return -1;
     if (paired(sy, h->precision, h->flags)) return 0;  // the mixed-size kernel
     if (!streamed(sy, h->precision, h->flags)) return sy.L;
@@ -354,6 +354,8 @@ int plan(mp_state* h, const mp_config* cfg) {
   }
   // streamed sizes mixed, or streamed with in-place ones: the streamed kernel runs both
   if (variant == 0 && all_streamed) variant = -2;
+  // Ising sizes mixed (batches are all Ising or all Heisenberg): the kernel for any L
+  if (variant == 0 && h->systems[0].lattice == MP_LATTICE_ISING) variant = kIsingKernel;
   h->variant = variant;
   int sms = 0, smem_max = 0, cta_max = 0;
   MP_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
@@ -452,7 +454,9 @@ int plan(mp_state* h, const mp_config* cfg) {
     tp[k] = t;
     // partial-sum ring: the largest power of two up to 16 sweeps that fits
     ring[k] = 16;
-    const int64_t lat = lattice_bytes(h->systems[k], real);
+    // shared-memory bytes of the lattice (Ising: with a copy of each boundary row)
+    const int64_t lat = h->systems[k].lattice == MP_LATTICE_ISING ? ising_slice_spin_bytes(h->systems[k].L)
+                                                                   : lattice_bytes(h->systems[k], real);
     pick_ring(ring[k], slice[k], [&]() {
       return static_cast<int>(std::min<int64_t>(INT32_MAX / 2, round_up(slice_spin_offset(t, ring[k]) + lat, 128)));
     }, t);
@@ -779,12 +783,16 @@ std::vector<int> tp_candidates(mp_state* h, int k, int cta_max) {
     for (int r : {2, 4, 8}) add(std::max(HL, HL * ((sy.L + r - 1) / r)));
     return c;
   }
-  // every multiple of 32 with 2 .. 48 sites per thread (at most 16 with
-  // 512-thread CTAs): the column-segment walk runs any of them, and how well
-  // a count splits the columns is easier to measure than to model
+  // every multiple of 32 with 2 .. 48 sites per thread: the column-segment
+  // walk runs any of them, and how well a count splits the columns is easier
+  // to measure than to model.  Ising paths also try up to 64 sites per thread:
+  // their lattices are bytes, so one warp per path (synchronised by
+  // __syncwarp instead of a named barrier) fits 32 paths into a CTA, which at
+  // L = 60 beats every wider layout.
+  const double max_sites = sy.lattice == MP_LATTICE_ISING ? 64.0 : 48.0;
   for (int t = 32; t <= std::min(cta_max, NH); t += 32) {
     const double sites = static_cast<double>(NH) / t;
-    if (sites >= 2.0 && sites <= 48.0) add(t);
+    if (sites >= 2.0 && sites <= max_sites) add(t);
   }
   return c;
 }
