@@ -242,8 +242,8 @@ def test_status_codes():
     with pytest.raises(mp.MPError) as ei:
         mp.Simulation([mp.System(4, 1.0)], 1, 0)
     assert ei.value.status == mp.MP_EINVAL
-    with pytest.raises(mp.MPError) as ei:
-        mp.Simulation([mp.System(64, 1.0)], 1, 1, precision=mp.FP64)
+    with pytest.raises(mp.MPError) as ei:  # L = 32 runs on two-CTA clusters of 512 threads
+        mp.Simulation([mp.System(32, 1.0)], 1, 1, cta_threads=256)
     assert ei.value.status == mp.MP_EINVAL
     sim = mp.Simulation([mp.System(4, 1.0, n_paths=4)], 1, 1)
     with pytest.raises(mp.MPError) as ei:
