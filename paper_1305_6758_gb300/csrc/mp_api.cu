@@ -715,8 +715,11 @@ int upload_tables(mp_state* h, const std::vector<WorkItem>& items, bool with_pai
 }
 
 // Throughput (attempts per ms) of system k under the current plan: one wave
-// of its work items through the real sweep kernel, with enough sweeps for
-// about 2e8 attempts.  Returns < 0 on error.
+// of its work items through the real sweep kernel, timed for s and for 2 s
+// sweeps (about 1e8 attempts per s); the difference leaves out what does not
+// scale with the sweeps (launch, initial state, records), which would
+// otherwise favour layouts whose wave holds fewer paths.  Returns < 0 on
+// error.
 double calibrate(mp_state* h, int k) {
   std::vector<WorkItem> sub;
   int64_t paths = 0;
@@ -728,7 +731,7 @@ double calibrate(mp_state* h, int k) {
   }
   if (sub.empty() || upload_tables(h, sub, false) != MP_OK || ensure_lattice(h) != MP_OK) return -1.0;
   const double per_sweep = static_cast<double>(paths) * h->hsys[k].N;
-  const int64_t sweeps = std::max<int64_t>(2, std::min<int64_t>(512, static_cast<int64_t>(2e8 / per_sweep)));
+  const int64_t s1 = std::max<int64_t>(2, std::min<int64_t>(256, static_cast<int64_t>(1e8 / per_sweep)));
   SweepParams p{};
   p.systems = h->d_sys;
   p.items = h->d_items;
@@ -736,35 +739,41 @@ double calibrate(mp_state* h, int k) {
   p.records = h->d_rec;
   p.n_items = static_cast<int32_t>(sub.size());
   p.init_mode = h->init_mode | ((h->flags & MP_FLAG_TWO_START) ? kTwoStart : 0);
-  // half thermalisation, half measurement sweeps, like a typical run
-  p.n_therm = sweeps / 2;
-  p.n_meas = sweeps - sweeps / 2;
   p.s_begin = 0;
-  p.s_end = sweeps;
   p.key = philox_round_keys(h->seed);
   p.lattice = h->d_lattice;
   p.lattice_stride = h->lattice_stride;
   p.lattice_groups = h->lattice_groups;
   p.error = h->d_error;
   p.ising_thr = h->d_thr;
-  // the faster of two timed launches (the first also warms the kernel up)
-  float best = 0.f;
-  for (int rep = 0; rep < 2; ++rep) {
-    float ms = 0.f;
-    if (cudaMemsetAsync(h->d_queue, 0, sizeof(int), h->stream) != cudaSuccess ||
-        cudaMemsetAsync(h->d_error, 0, sizeof(int), h->stream) != cudaSuccess ||
-        cudaEventRecord(h->ev[0], h->stream) != cudaSuccess ||
-        launch_sweep(h->precision, h->variant, p, std::min<int>(h->grid, static_cast<int>(sub.size())),
-                     h->cta, h->smem, h->stream) != cudaSuccess ||
-        cudaEventRecord(h->ev[1], h->stream) != cudaSuccess ||
-        cudaEventSynchronize(h->ev[1]) != cudaSuccess ||
-        cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]) != cudaSuccess) {
-      cudaGetLastError();
-      return -1.0;
+  // the faster of two timed launches of `sweeps` sweeps (half thermalisation,
+  // half measurement, like a typical run); < 0 on error
+  auto timed = [&](int64_t sweeps) -> float {
+    p.n_therm = sweeps / 2;
+    p.n_meas = sweeps - sweeps / 2;
+    p.s_end = sweeps;
+    float best = -1.f;
+    for (int rep = 0; rep < 2; ++rep) {
+      float ms = 0.f;
+      if (cudaMemsetAsync(h->d_queue, 0, sizeof(int), h->stream) != cudaSuccess ||
+          cudaMemsetAsync(h->d_error, 0, sizeof(int), h->stream) != cudaSuccess ||
+          cudaEventRecord(h->ev[0], h->stream) != cudaSuccess ||
+          launch_sweep(h->precision, h->variant, p, std::min<int>(h->grid, static_cast<int>(sub.size())),
+                       h->cta, h->smem, h->stream) != cudaSuccess ||
+          cudaEventRecord(h->ev[1], h->stream) != cudaSuccess ||
+          cudaEventSynchronize(h->ev[1]) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]) != cudaSuccess) {
+        cudaGetLastError();
+        return -1.f;
+      }
+      if (best < 0.f || ms < best) best = ms;
     }
-    if (rep == 0 || ms < best) best = ms;
-  }
-  return per_sweep * sweeps / std::max(best, 1e-3f);
+    return best;
+  };
+  const float t1 = timed(s1), t2 = timed(2 * s1);
+  if (t1 < 0.f || t2 < 0.f) return -1.0;
+  if (t2 <= t1) return per_sweep * 2 * s1 / std::max(t2, 1e-3f);  // too short to separate
+  return per_sweep * s1 / (t2 - t1);
 }
 
 // Threads-per-path candidates of system k for the autotuner.
