@@ -120,14 +120,14 @@ BYTES_PER_ATTEMPT_FP32 = 24
 # with this hash (sha256 over csrc/, first 16 hex digits); any change of the
 # sources voids it and the roofline reports traffic null.  Each is the timed
 # launch of the workload's bench command, captured at full size (one ncu pass):
-# sc16 reads 0.75 MB (tables; the lattices stay in shared memory), large moves
-# 28.94 TB against 28.99 TB of algorithmic bytes, batched 328 GB (its streamed
-# L = 32 lattices, 402 GB algorithmic, partly served from L2), ising 0.50 MB.
+# sc16 reads 0.88 MB (tables; the lattices stay in shared memory), batched
+# 0.90 MB (every size, L = 32 included, stays in shared memory), large moves
+# 28.96 TB against 28.99 TB of algorithmic bytes, ising 0.99 MB.
 TRAFFIC = {
-    "sc16": {"sources": "1353bf33dc85ee14", "bytes": 0.746e6},
-    "large": {"sources": "1353bf33dc85ee14", "bytes": 14.44e12 + 14.50e12},
-    "batched": {"sources": "1353bf33dc85ee14", "bytes": 129.70e9 + 198.21e9},
-    "ising": {"sources": "1353bf33dc85ee14", "bytes": 0.501e6},
+    "sc16": {"sources": "85a1ad5606aea8f6", "bytes": 0.880128e6},
+    "large": {"sources": "85a1ad5606aea8f6", "bytes": 14.462353e12 + 14.501406e12},
+    "batched": {"sources": "85a1ad5606aea8f6", "bytes": 0.904192e6},
+    "ising": {"sources": "85a1ad5606aea8f6", "bytes": 0.992256e6 + 256},
 }
 
 
@@ -537,9 +537,9 @@ def main():
                 s2.estimates(j)
             plan = s2.plan()
         e2e_s.append(time.perf_counter() - t0)
-    # the caller's system table, then the library's DevSystem (88 B), WorkItem
+    # the caller's system table, then the library's DevSystem (96 B), WorkItem
     # (16 B), spin-offset (8 B) and Ising-threshold (80 B) tables
-    h2d_total = (ctypes.sizeof(mp.MPSystem) + 88 + 8 + 80) * n_sys + 16 * plan["n_items"]
+    h2d_total = (ctypes.sizeof(mp.MPSystem) + 96 + 8 + 80) * n_sys + 16 * plan["n_items"]
     d2h_total = ctypes.sizeof(mp.MPEstimates) * n_sys
     e2e_value = attempts_rank * world / (sum(e2e_s) / len(e2e_s))
 
