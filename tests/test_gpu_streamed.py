@@ -214,3 +214,28 @@ def test_fp32_mixed_kernel_follows_the_single_size_kernel(L):
     a, _ = gpu_records(alone, 3, 4, seed=12)
     b, _ = gpu_records(alone + [mp.System(8, 1.0, n_paths=7)], 3, 4, seed=12)
     np.testing.assert_allclose(b[0][:, FIELDS], a[0][:, FIELDS], rtol=2e-6, atol=2e-7)
+
+
+def test_in_place_split_schedule_and_spins():
+    """The in-place HBM path (FP64 L = 46) through resumable runs: a schedule
+    split by a checkpoint equals one run, and the final spins equal the
+    oracle's after one sweep."""
+    systems = [mp.System(46, 1.1, n_paths=2)]
+    with mp.Simulation(systems, 2, 2, seed=3, precision=mp.FP64) as whole:
+        whole.run_sweeps(4)
+        ref = whole.paths(0)
+    with mp.Simulation(systems, 2, 2, seed=3, precision=mp.FP64) as a:
+        a.run_sweeps(3)
+        blob = a.checkpoint()
+    with mp.Simulation(systems, 2, 2, seed=3, precision=mp.FP64) as b:
+        b.restore(blob)
+        b.run_sweeps(1)
+        got = b.paths(0)
+    np.testing.assert_allclose(got[:, FIELDS], ref[:, FIELDS], rtol=1e-12, atol=1e-14)
+    np.testing.assert_array_equal(got[:, 17], ref[:, 17])
+    with mp.Simulation(systems, 0, 1, seed=3, precision=mp.FP64, keep_spins=True) as sim:
+        sim.run()
+        spins = [sim.spins(0, p) for p in range(2)]
+    _, ospins = O.run([osys(systems[0])], 0, 1, seed=3, want_spins=True)
+    for p in range(2):
+        np.testing.assert_allclose(spins[p].reshape(-1, 3), ospins[0][p], rtol=0, atol=1e-12)
