@@ -137,3 +137,22 @@ def test_cluster_cancel_stops_both_ctas():
     with mp.Simulation([mp.System(32, 1.5, n_paths=4)], 2, 2) as ok:
         ok.run()
         assert np.isfinite(ok.estimates(0)["e"])
+
+
+def test_every_lattice_mode_in_one_launch():
+    """One FP32 batch with a lattice of each mode (two-CTA cluster L = 32,
+    streamed L = 64, in place L = 66, shared memory L = 8): the mixed-size
+    kernel, launched in clusters, dispatches each; every path against the
+    oracle after two sweeps (a borderline acceptance may flip one path)."""
+    systems = [mp.System(32, 1.4, n_paths=3), mp.System(64, 1.44, n_paths=2), mp.System(66, 1.5, n_paths=2),
+               mp.System(8, 1.0, n_paths=5)]
+    with mp.Simulation(systems, 1, 1, seed=14) as sim:
+        sim.run()
+        plans = [sim.system_plan(k) for k in range(len(systems))]
+        got = [sim.paths(k) for k in range(len(systems))]
+    assert plans[0]["cluster_pair"] and plans[1]["streamed"] and plans[2]["in_place_hbm"]
+    assert not (plans[3]["cluster_pair"] or plans[3]["streamed"] or plans[3]["in_place_hbm"])
+    refs = O.run([osys(s) for s in systems], 1, 1, seed=14)
+    for s, g, r in zip(systems, got, refs):
+        bad = sum(int(np.max(np.abs(a[FIELDS] - b[FIELDS])) > 1e-5) for a, b in zip(g, r))
+        assert bad <= 1, (s.L, bad)
