@@ -330,19 +330,21 @@ __device__ __forceinline__ void attempt(uint32_t i, const PhiloxPrefix& pre, con
 // chains), the chunk U: every segment is a whole number of chunks (the
 // segment count K is restricted to divisors of L whose segment length L/K is
 // a multiple of U), so no site is left to a serial remainder loop.  FP32
-// kernels (512-thread CTAs, up to 128 registers per thread): 8 for L = 16,
-// 6 for 12, 18 and 24, 4 for 8 and 20, 7 for 14, 3 for 6, 2 for 10, 22 and 26,
-// 1 for 2 and 4 (whose columns are too short to split into chunks).  The
-// mixed-size kernel holds every size's walk in one register allocation and
-// takes 3 for 12, 18, 24 and 2 for 14, which keep it within 128 registers
-// without spills.  FP64 kernels (64 registers per thread) take one site at a
-// time.  Measured on the benchmark layouts: chunks of 2 lose 6% against 4, 8
-// gains 1% over 4 at L = 16, 16 spills; whole chunks of 6 gain 6-8% over a
-// runtime unroll of 4 at L = 12, 18, 24.
+// kernels (512-thread CTAs, up to 128 registers per thread): 8 for L = 8 and
+// 16 (a whole column at L = 8), 6 for 12, 18 and 24, 4 for 20, 7 for 14, 3 for
+// 6, 2 for 10, 22 and 26, 1 for 2 and 4 (whose columns are too short to split
+// into chunks).  The mixed-size kernel holds every size's walk in one register
+// allocation and takes 3 for 12 and 18 and 2 for 14, which keep it within 128
+// registers without spills, and 6 for 24.  FP64 kernels (64 registers per
+// thread) take one site at a time.  Measured on the benchmark layouts: chunks
+// of 2 lose 6% against 4, 8 gains 1% over 4 at L = 16, 16 spills; whole chunks
+// of 6 gain 6-8% over a runtime unroll of 4 at L = 12, 18, 24; in the batch of
+// uneven sizes, 8 at L = 8 and 6 at L = 24 gain 1.3% together, while 6 at
+// L = 12 loses 1%.
 constexpr int column_chunk_fp32(int L, bool mixed) {
-  return L == 16                   ? 8
-         : (L % 6 == 0 && L >= 12) ? (mixed ? 3 : 6)
-         : (L == 8 || L == 20)     ? 4
+  return (L == 16 || L == 8)       ? 8
+         : (L % 6 == 0 && L >= 12) ? ((mixed && L < 24) ? 3 : 6)
+         : L == 20                 ? 4
          : L == 14                 ? (mixed ? 2 : 7)
          : L == 6                  ? 3
          : L <= 4                  ? 1
