@@ -401,11 +401,10 @@ int mp_philox(const uint32_t* d_ctr, int64_t n, uint64_t seed, uint32_t* d_out, 
  * process exits.  Limits: at most MP_NOALLOC_MAX_PATHS paths in total and
  * MP_NOALLOC_MAX_SYSTEMS systems; larger batches return MP_EINVAL before any
  * GPU work.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array and it keeps the
- * last call's contents (the work counter is cleared at the start of each
- * call): calls whose GPU work overlaps, on different streams or different
- * host threads, race on it.  Errors: MP_EINVAL (NULL pointer, bad sizes,
+ * (cudaGetSymbolAddress) with that device current.  All calls share the
+ * one array and it keeps the last call's contents (the work counter is
+ * cleared at the start of each call): calls whose GPU work overlaps, on
+ * different streams or different host threads, race on it.  Errors: MP_EINVAL (NULL pointer, bad sizes,
  * unsupported lattice), MP_ECUDA (device error). */
 #define MP_NOALLOC_MAX_PATHS 16384
 #define MP_NOALLOC_MAX_SYSTEMS 64
