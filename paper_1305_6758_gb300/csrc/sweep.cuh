@@ -384,35 +384,53 @@ __device__ __forceinline__ void half_sweep(const Geom& geo, int c, const PhiloxP
     if (K > 0) {
       constexpr int HL = Geom::HL, HP = Geom::HP, LL = 2 * Geom::HL;
       const int seg = LL / K;  // planes per segment
+      constexpr int U = kColumnChunk<Real, Geom>;
       for (int u = tid; u < HP * K; u += tp) {
-        const int g = u / HP;
-        const int col = u - g * HP;
+        // u >= 0: unsigned division by the compile-time HP and HL needs no
+        // sign fix-up
+        const unsigned uu = static_cast<unsigned>(u);
+        const int g = static_cast<int>(uu / HP);
+        const int col = static_cast<int>(uu % HP);
         const int z0 = g * seg;
-        const int hx = col % HL;
-        const int y = col / HL;
+        const int hx = static_cast<int>(static_cast<unsigned>(col) % HL);
+        const int y = static_cast<int>(static_cast<unsigned>(col) / HL);
         const int oyp = (y == LL - 1) ? -(LL - 1) * HL : HL;
         const int oym = (y == 0) ? (LL - 1) * HL : -HL;
         const int oxp1 = (hx == HL - 1) ? -(HL - 1) : 1;  // +x offset when x is odd
         const int oxm0 = (hx == 0) ? (HL - 1) : -1;         // -x offset when x is even
-        constexpr int U = kColumnChunk<Real, Geom>;
+        // The x parity p of the site flips from plane to plane: sites an even
+        // number of planes after the chunk's first take (pa, oxa), the others
+        // (pb, oxb), so within a chunk the choice is made at compile time.
+        int pa = (y + z0 + c) & 1;
+        int pb = pa ^ 1;
+        int oxa = pa ? oxp1 : oxm0;
+        int oxb = pa ? oxm0 : oxp1;
+        const int oxx = oxa ^ oxb;
         int hh = col + HP * z0;
         V3<Real> o0 = oth.ld(hh);  // the other colour at the site's half index
         V3<Real> mz = oth.ld(z0 == 0 ? hh + (LL - 1) * HP : hh - HP);  // -z neighbour
-        // segments are whole chunks: with that hint the compiler leaves out the
-        // remainder loop; at L = 16 (chunks of 8) the kernel fits 128
-        // registers without spills only without it
-        if constexpr (U != 8) __builtin_assume(seg % U == 0);
-#pragma unroll(U)
-        for (int z = z0; z < z0 + seg; ++z, hh += HP) {
-          const int p = (y + z + c) & 1;
-          const int nxo = hh + (p ? oxp1 : oxm0);
-          const V3<Real> cz = oth.ld(z == LL - 1 ? hh - (LL - 1) * HP : hh + HP);
-          const V3<Real> f =
-              add3(add3(add3(add3(add3(o0, oth.ld(nxo)), oth.ld(hh + oyp)), oth.ld(hh + oym)), cz), mz);
-          update<Real, kMeas, kEnergy>(static_cast<uint32_t>(2 * hh + p), pre, key, own, hh,
-                                       f.x, f.y, f.z, J, hf, bp, accepted, part);
-          mz = o0;
-          o0 = cz;
+        for (int zc = z0; zc < z0 + seg; zc += U) {
+#pragma unroll
+          for (int k = 0; k < U; ++k, hh += HP) {
+            const int p = (k & 1) ? pb : pa;
+            const int nxo = hh + ((k & 1) ? oxb : oxa);
+            // chunks start at multiples of U, which divides L: only a chunk's
+            // last plane can be plane L - 1, whose +z neighbour wraps
+            const int zn = (k == U - 1 && zc + k == LL - 1) ? hh - (LL - 1) * HP : hh + HP;
+            const V3<Real> cz = oth.ld(zn);
+            const V3<Real> f =
+                add3(add3(add3(add3(add3(o0, oth.ld(nxo)), oth.ld(hh + oyp)), oth.ld(hh + oym)), cz), mz);
+            update<Real, kMeas, kEnergy>(static_cast<uint32_t>(2 * hh + p), pre, key, own, hh,
+                                         f.x, f.y, f.z, J, hf, bp, accepted, part);
+            mz = o0;
+            o0 = cz;
+          }
+          if constexpr (U & 1) {  // an odd chunk: the next one starts on the other parity
+            pa ^= 1;
+            pb ^= 1;
+            oxa ^= oxx;
+            oxb ^= oxx;
+          }
         }
       }
       return;
