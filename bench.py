@@ -535,11 +535,11 @@ def main():
             s2.run()
             for j in range(n_sys):
                 s2.estimates(j)
-            plan = s2.plan()
+            upload = s2.upload_bytes()
         e2e_s.append(time.perf_counter() - t0)
-    # the caller's system table, then the library's DevSystem (96 B), WorkItem
-    # (16 B), spin-offset (8 B) and Ising-threshold (80 B) tables
-    h2d_total = (ctypes.sizeof(mp.MPSystem) + 96 + 8 + 80) * n_sys + 16 * plan["n_items"]
+    # the caller's system table, then the library's plan tables (systems, work
+    # items, offsets, Ising thresholds, column-walk units) as the library counts them
+    h2d_total = ctypes.sizeof(mp.MPSystem) * n_sys + upload
     d2h_total = ctypes.sizeof(mp.MPEstimates) * n_sys
     e2e_value = attempts_rank * world / (sum(e2e_s) / len(e2e_s))
 

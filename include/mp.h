@@ -308,6 +308,12 @@ int mp_timing(mp_handle h, double* sweep_ms, double* reduce_ms);
  * NULL. */
 int mp_plan(mp_handle h, int* cta_threads, int* grid, int* smem_bytes, int* n_items);
 
+/* Bytes of the plan's tables (systems, work items, offsets, Ising thresholds,
+ * column-walk units) that the handle last copied from host to device: once
+ * when it is created, for the plan its runs then use.  Errors: MP_EINVAL
+ * (NULL handle or output). */
+int mp_upload_bytes(mp_handle h, int64_t* bytes);
+
 /* Resumable runs.  mp_run_sweeps advances every path of every system by
  * n_sweeps sweeps of its schedule (n_therm thermalisation sweeps, then n_meas
  * measurement sweeps) from its saved state -- the initial state on the first

@@ -101,7 +101,7 @@ assert ctypes.sizeof(MPEstimates) == NEST * 8
 # Every symbol include/mp.h declares.
 EXPORTS = [
     "mp_create", "mp_create_ex", "mp_run", "mp_set_seed", "mp_estimates", "mp_paths",
-    "mp_device_buffers", "mp_spins", "mp_backward", "mp_timing", "mp_plan", "mp_system_plan",
+    "mp_device_buffers", "mp_spins", "mp_backward", "mp_timing", "mp_plan", "mp_upload_bytes", "mp_system_plan",
     "mp_run_sweeps", "mp_progress", "mp_checkpoint", "mp_restore", "mp_cancel", "mp_philox",
     "mp_reduce", "mp_destroy", "mp_last_error", "mp_status_string",
 ]
@@ -133,6 +133,7 @@ def load_library(path: str = LIB_PATH):
     lib.mp_backward.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.mp_timing.argtypes = [H, P(dbl), P(dbl)]
     lib.mp_plan.argtypes = [H] + [P(ctypes.c_int)] * 4
+    lib.mp_upload_bytes.argtypes = [H, P(i64)]
     lib.mp_system_plan.argtypes = [H, ctypes.c_int] + [P(ctypes.c_int)] * 3
     lib.mp_run_sweeps.argtypes = [H, i64]
     lib.mp_progress.argtypes = [H, P(i64)]
@@ -338,6 +339,12 @@ class Simulation:
         v = [ctypes.c_int() for _ in range(4)]
         _check(_lib.mp_plan(self._h, *[ctypes.byref(x) for x in v]), self._h)
         return dict(cta_threads=v[0].value, grid=v[1].value, smem_bytes=v[2].value, n_items=v[3].value)
+
+    def upload_bytes(self) -> int:
+        """Bytes of plan tables the handle copied from host to device when it was created."""
+        b = ctypes.c_int64()
+        _check(_lib.mp_upload_bytes(self._h, ctypes.byref(b)), self._h)
+        return b.value
 
     def run_sweeps(self, n: int):
         """Advance every path by n sweeps of its schedule from its saved state (synchronous)."""

@@ -2,6 +2,8 @@
 #pragma once
 #include <cstdint>
 
+#include <vector_types.h>
+
 #include "mp.h"
 #include "philox.cuh"
 
@@ -40,8 +42,10 @@ struct DevSystem {
   int64_t rec_offset;   // global index of this system's path 0
   int64_t n_paths;
   int32_t mode;         // kModeShared / kModeStreamed / kModePair / kModeGlobal
-  int32_t pad;
+  int32_t unit_K;       // column segments per column of the unit table (below)
   int64_t path_begin;   // path id (random-number counter) of the system's path 0
+  int32_t unit_off;     // first entry of the system's column-walk units in SweepParams::units, or -1
+  int32_t unit_U;       // column chunk the unit table was made for
 };
 
 constexpr int kModeShared = 0;
@@ -97,7 +101,91 @@ struct SweepParams {
   const WorkItem* pair_items;
   int32_t n_pair_items;
   int* pair_queue;
+  // Column-walk units of the simple cubic lattices in shared memory (see
+  // column_unit), made by the host for each system's threads per path; a
+  // system without one (unit_off < 0) derives its units on the device.
+  const int4* units;
 };
+
+// ----------------------------------------------------- column-walk plan --
+// The shared-memory walk of a simple cubic lattice takes a colour's sites as
+// L^2/2 columns of L planes, each cut into K segments of L/K planes that are
+// walked in unrolled chunks of U planes.
+
+// Planes of a column segment interleaved by the compiler (independent Philox
+// chains), the chunk U: every segment is a whole number of chunks (the
+// segment count K is restricted to divisors of L whose segment length L/K is
+// a multiple of U), so no site is left to a serial remainder loop.  FP32
+// kernels (512-thread CTAs, up to 128 registers per thread): 8 for L = 8 and
+// 16 (a whole column at L = 8), 6 for 12, 18 and 24, 4 for 20, 7 for 14, 3 for
+// 6, 2 for 10, 22 and 26, 1 for 2 and 4 (whose columns are too short to split
+// into chunks).  The mixed-size kernel holds every size's walk in one register
+// allocation and takes 3 for 12 and 18 and 2 for 14, which keep it within 128
+// registers without spills, and 6 for 24.  FP64 kernels (64 registers per
+// thread) take one site at a time.  Measured on the benchmark layouts: chunks
+// of 2 lose 6% against 4, 8 gains 1% over 4 at L = 16, 16 spills; whole chunks
+// of 6 gain 6-8% over a runtime unroll of 4 at L = 12, 18, 24; in the batch of
+// uneven sizes, 8 at L = 8 and 6 at L = 24 gain 1.3% together, while 6 at
+// L = 12 loses 1%.
+__host__ __device__ constexpr int column_chunk_fp32(int L, bool mixed) {
+  return (L == 16 || L == 8)       ? 8
+         : (L % 6 == 0 && L >= 12) ? ((mixed && L < 24) ? 3 : 6)
+         : L == 20                 ? 4
+         : L == 14                 ? (mixed ? 2 : 7)
+         : L == 6                  ? 3
+         : L <= 4                  ? 1
+                                   : 2;
+}
+__host__ __device__ constexpr int column_chunk(int real_bytes, int L, bool mixed) {
+  return real_bytes == 8 ? 1 : column_chunk_fp32(L, mixed);
+}
+
+// Column segments per column: the divisor K of L, with segments of whole
+// chunks, that spreads the (L^2/2) K units most evenly over the tp threads
+// (the smallest such K, for the longest segments).
+__host__ __device__ inline int column_segments(int L, int U, int tp) {
+  const int HP = L * L / 2;
+  int K = 1;
+  double best = -1.0;
+  for (int k = 1; k <= L; ++k) {
+    if (L % k || (L / k) % U) continue;
+    const int units = HP * k;
+    const double eff = static_cast<double>(units) / (static_cast<double>((units + tp - 1) / tp) * tp);
+    if (eff > best + 1e-9) {
+      best = eff;
+      K = k;
+    }
+  }
+  return K;
+}
+
+// Unit u = g HP + col (column col = x/2 + (L/2) y, segment g of planes
+// z0 .. z0 + L/K - 1) as the walk of colour 0 needs it: x = half index of its
+// first site | (x parity of that site) << 31; y = half index of that site's
+// -z neighbour (bits 0..15) | +-x offset of the sites an even number of
+// planes into a chunk (signed, bits 16..23) | the same for the others
+// (bits 24..31); z, w = +y and -y offsets.  Colour 1 flips the parity and
+// swaps the two x offsets.
+__host__ __device__ inline int4 column_unit(int L, int K, int u) {
+  const int HL = L / 2, HP = L * L / 2, seg = L / K;
+  const int g = u / HP, col = u % HP, z0 = g * seg;
+  const int hx = col % HL, y = col / HL;
+  const int oyp = (y == L - 1) ? -(L - 1) * HL : HL;
+  const int oym = (y == 0) ? (L - 1) * HL : -HL;
+  const int oxp1 = (hx == HL - 1) ? -(HL - 1) : 1;  // +x offset when x is odd
+  const int oxm0 = (hx == 0) ? (HL - 1) : -1;         // -x offset when x is even
+  const int pa = (y + z0) & 1;
+  const int oxa = pa ? oxp1 : oxm0, oxb = pa ? oxm0 : oxp1;
+  const int hh = col + HP * z0;
+  const int mz = z0 == 0 ? hh + (L - 1) * HP : hh - HP;
+  int4 d;
+  d.x = static_cast<int>(static_cast<unsigned>(hh) | (static_cast<unsigned>(pa) << 31));
+  d.y = static_cast<int>(static_cast<unsigned>(mz) | (static_cast<unsigned>(oxa & 0xff) << 16) |
+                        (static_cast<unsigned>(oxb & 0xff) << 24));
+  d.z = oyp;
+  d.w = oym;
+  return d;
+}
 
 constexpr int kErrTimeout = 1;
 constexpr int kErrCanceled = 2;

@@ -15,6 +15,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "kernels.h"
@@ -165,6 +166,9 @@ struct mp_state {
   double* d_spins = nullptr;
   int64_t* d_spin_offset = nullptr;
   unsigned long long* d_thr = nullptr;  // Ising acceptance thresholds, 10 per system
+  int4* d_units = nullptr;         // column-walk unit tables (column_unit), one per (L, K, U)
+  int64_t units_capacity = 0;      // entries allocated at d_units
+  int64_t upload_bytes = 0;        // bytes the last upload_tables copied to the device
   double* d_sort = nullptr;        // sort space of the distribution coefficient (systems > 16384 paths)
   int* d_error = nullptr;          // nonzero when a bounded wait in a kernel gave up
   void* d_lattice = nullptr;       // HBM lattices of streamed paths
@@ -523,7 +527,9 @@ int plan(mp_state* h, const mp_config* cfg) {
     d.mode = paired(s, h->precision, h->flags) ? kModePair
              : global(s)                         ? kModeGlobal
              : streamed(s, h->precision, h->flags) ? kModeStreamed : kModeShared;
-    d.pad = 0;
+    d.unit_K = 0;  // unit tables are made when the plan's tables are uploaded
+    d.unit_off = -1;
+    d.unit_U = 0;
     if (d.mode == kModeStreamed) {
       h->lattice_groups = std::max(h->lattice_groups, d.g);
       h->lattice_stride = std::max<int64_t>(
@@ -637,6 +643,7 @@ int enqueue_run(mp_state* h, int64_t s_begin, int64_t s_end, bool resume, bool s
   p.lattice_groups = h->lattice_groups;
   p.error = h->d_error;
   p.ising_thr = h->d_thr;
+  p.units = h->d_units;
   p.test_stall = (h->flags & MP_FLAG_TEST_STALL) ? 1u : 0u;
   p.s_begin = s_begin;
   p.s_end = s_end;
@@ -695,22 +702,53 @@ int ensure_lattice(mp_state* h) {
 // paths for two-CTA clusters (with_pairs).
 int upload_tables(mp_state* h, const std::vector<WorkItem>& items, bool with_pairs) {
   const int n = static_cast<int>(h->hsys.size());
-  MP_CUDA(h, cudaMemcpyAsync(h->d_sys, h->hsys.data(), sizeof(DevSystem) * n, cudaMemcpyHostToDevice,
-                             h->stream));
-  if (!items.empty())
-    MP_CUDA(h, cudaMemcpyAsync(h->d_items, items.data(), sizeof(WorkItem) * items.size(),
-                               cudaMemcpyHostToDevice, h->stream));
+  // The column-walk units of the simple cubic lattices in shared memory, one
+  // table per (L, K, U) shared by every system with those values: the host
+  // decodes each unit once instead of every thread at every half-sweep.  U is
+  // the chunk of the kernel the plan launches (the mixed-size kernel's for a
+  // batch of uneven sizes); a system left without a table derives its units
+  // on the device.
+  std::vector<int4> units;
+  std::map<std::tuple<int, int, int>, int> unit_at;
+  const bool mixed = h->variant == 0;
+  const int real = h->precision == MP_FP64 ? 8 : 4;
+  for (int k = 0; k < n; ++k) {
+    DevSystem& d = h->hsys[k];
+    d.unit_off = -1;
+    d.unit_K = 0;
+    d.unit_U = 0;
+    if (h->variant == kRandomSiteKernel || d.lattice != MP_LATTICE_SC || d.mode != kModeShared) continue;
+    const int U = column_chunk(real, d.L, mixed);
+    if (d.L % U != 0) continue;
+    const int K = column_segments(d.L, U, d.tp);
+    const int n_units = d.L * d.L / 2 * K;
+    auto it = unit_at.find(std::make_tuple(d.L, K, U));
+    if (it == unit_at.end()) {
+      if (static_cast<int64_t>(units.size()) + n_units > h->units_capacity) continue;
+      it = unit_at.emplace(std::make_tuple(d.L, K, U), static_cast<int>(units.size())).first;
+      for (int u = 0; u < n_units; ++u) units.push_back(column_unit(d.L, K, u));
+    }
+    d.unit_off = it->second;
+    d.unit_K = K;
+    d.unit_U = U;
+  }
+  int64_t bytes = 0;
+  auto copy = [&](void* dst, const void* src, size_t b) {
+    bytes += static_cast<int64_t>(b);
+    return cudaMemcpyAsync(dst, src, b, cudaMemcpyHostToDevice, h->stream);
+  };
+  MP_CUDA(h, copy(h->d_sys, h->hsys.data(), sizeof(DevSystem) * n));
+  if (!items.empty()) MP_CUDA(h, copy(h->d_items, items.data(), sizeof(WorkItem) * items.size()));
   if (with_pairs && !h->pair_items.empty())
-    MP_CUDA(h, cudaMemcpyAsync(h->d_items + items.size(), h->pair_items.data(),
-                               sizeof(WorkItem) * h->pair_items.size(), cudaMemcpyHostToDevice, h->stream));
-  MP_CUDA(h, cudaMemcpyAsync(h->d_spin_offset, h->spin_offset.data(), sizeof(int64_t) * n,
-                             cudaMemcpyHostToDevice, h->stream));
+    MP_CUDA(h, copy(h->d_items + items.size(), h->pair_items.data(), sizeof(WorkItem) * h->pair_items.size()));
+  MP_CUDA(h, copy(h->d_spin_offset, h->spin_offset.data(), sizeof(int64_t) * n));
   std::vector<unsigned long long> thr(10 * static_cast<size_t>(n), 0ull);
   for (int k = 0; k < n; ++k)
     if (h->systems[k].lattice == MP_LATTICE_ISING) ising_thresholds(h->systems[k], &thr[10 * k]);
-  MP_CUDA(h, cudaMemcpyAsync(h->d_thr, thr.data(), sizeof(unsigned long long) * thr.size(),
-                             cudaMemcpyHostToDevice, h->stream));
+  MP_CUDA(h, copy(h->d_thr, thr.data(), sizeof(unsigned long long) * thr.size()));
+  if (!units.empty()) MP_CUDA(h, copy(h->d_units, units.data(), sizeof(int4) * units.size()));
   MP_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->upload_bytes = bytes;
   return MP_OK;
 }
 
@@ -746,6 +784,7 @@ double calibrate(mp_state* h, int k) {
   p.lattice_groups = h->lattice_groups;
   p.error = h->d_error;
   p.ising_thr = h->d_thr;
+  p.units = h->d_units;
   // the faster of two timed launches of `sweeps` sweeps (half thermalisation,
   // half measurement, like a typical run); < 0 on error
   auto timed = [&](int64_t sweeps) -> float {
@@ -959,6 +998,12 @@ int mp_create_ex(const mp_config* cfg, mp_handle* out) {
   h->d_est = static_cast<double*>(dev_alloc(h, sizeof(double) * MP_NEST * n));
   h->d_spin_offset = static_cast<int64_t*>(dev_alloc(h, sizeof(int64_t) * n));
   h->d_thr = static_cast<unsigned long long*>(dev_alloc(h, sizeof(unsigned long long) * 10 * n));
+  // unit tables: at most L^3/2 units per simple cubic size that fits shared memory
+  h->units_capacity = 0;
+  for (const mp_system& s : h->systems)
+    if (s.lattice == MP_LATTICE_SC && s.L <= 26) h->units_capacity += static_cast<int64_t>(s.L) * s.L * s.L / 2;
+  h->d_units = h->units_capacity > 0 ? static_cast<int4*>(dev_alloc(h, sizeof(int4) * h->units_capacity)) : nullptr;
+  if (h->units_capacity > 0 && !h->d_units) h->units_capacity = 0;  // the device derives the units
   if (!h->d_sys || !h->d_items || !h->d_queue || !h->d_rec || !h->d_est || !h->d_spin_offset ||
       !h->d_thr)
     return bail(fail(h, MP_ENOMEM, "device allocation failed"));
@@ -1112,6 +1157,12 @@ int mp_plan(mp_handle h, int* cta_threads, int* grid, int* smem_bytes, int* n_it
   if (grid) *grid = h->grid;
   if (smem_bytes) *smem_bytes = h->smem;
   if (n_items) *n_items = static_cast<int>(h->items.size() + h->pair_items.size());
+  return MP_OK;
+}
+
+int mp_upload_bytes(mp_handle h, int64_t* bytes) {
+  if (!h || !bytes) return fail(h, MP_EINVAL, "handle or output is NULL");
+  *bytes = h->upload_bytes;
   return MP_OK;
 }
 

@@ -128,6 +128,7 @@ extern "C" int mp_run_noalloc(const mp_system* systems, int n_systems, int preci
     ds.rec_offset = rec;
     ds.n_paths = s.n_paths;
     ds.path_begin = s.path_begin;
+    ds.unit_off = -1;  // no unit tables: the column walk derives its units on the device
     for (int64_t p = 0; p < s.n_paths; ++p) g_items[n_items++] = WorkItem{k, 1, p};
     rec += s.n_paths;
     cta = std::max(cta, tp);

@@ -326,33 +326,9 @@ __device__ __forceinline__ void attempt(uint32_t i, const PhiloxPrefix& pre, con
                                part);
 }
 
-// Planes of a column segment interleaved by the compiler (independent Philox
-// chains), the chunk U: every segment is a whole number of chunks (the
-// segment count K is restricted to divisors of L whose segment length L/K is
-// a multiple of U), so no site is left to a serial remainder loop.  FP32
-// kernels (512-thread CTAs, up to 128 registers per thread): 8 for L = 8 and
-// 16 (a whole column at L = 8), 6 for 12, 18 and 24, 4 for 20, 7 for 14, 3 for
-// 6, 2 for 10, 22 and 26, 1 for 2 and 4 (whose columns are too short to split
-// into chunks).  The mixed-size kernel holds every size's walk in one register
-// allocation and takes 3 for 12 and 18 and 2 for 14, which keep it within 128
-// registers without spills, and 6 for 24.  FP64 kernels (64 registers per
-// thread) take one site at a time.  Measured on the benchmark layouts: chunks
-// of 2 lose 6% against 4, 8 gains 1% over 4 at L = 16, 16 spills; whole chunks
-// of 6 gain 6-8% over a runtime unroll of 4 at L = 12, 18, 24; in the batch of
-// uneven sizes, 8 at L = 8 and 6 at L = 24 gain 1.3% together, while 6 at
-// L = 12 loses 1%.
-constexpr int column_chunk_fp32(int L, bool mixed) {
-  return (L == 16 || L == 8)       ? 8
-         : (L % 6 == 0 && L >= 12) ? ((mixed && L < 24) ? 3 : 6)
-         : L == 20                 ? 4
-         : L == 14                 ? (mixed ? 2 : 7)
-         : L == 6                  ? 3
-         : L <= 4                  ? 1
-                                   : 2;
-}
+// The column chunk U of a geometry (column_chunk in common.cuh).
 template <typename Real, class Geom>
-constexpr int kColumnChunk =
-    sizeof(Real) == 8 ? 1 : column_chunk_fp32(2 * Geom::HL, Geom::kInMixed);
+constexpr int kColumnChunk = column_chunk(static_cast<int>(sizeof(Real)), 2 * Geom::HL, Geom::kInMixed);
 
 // One half-sweep of one thread: every site of colour c it owns.
 //
@@ -375,7 +351,7 @@ constexpr int kColumnChunk =
 template <typename Real, class Geom, bool kMeas, bool kEnergy>
 __device__ __forceinline__ void half_sweep(const Geom& geo, int c, const PhiloxPrefix& pre,
                                            const PhiloxKeys& key, Real* sp, int tid,
-                                           int tp, int K, Real J, Real hf, Real bp,
+                                           int tp, int K, const int4* units, Real J, Real hf, Real bp,
                                            int& accepted, Partials<Real>& part) {
   const int S = geo.stride();
   const SpinView<Real> own(sp + c * 3 * S, S);
@@ -385,38 +361,55 @@ __device__ __forceinline__ void half_sweep(const Geom& geo, int c, const PhiloxP
       constexpr int HL = Geom::HL, HP = Geom::HP, LL = 2 * Geom::HL;
       const int seg = LL / K;  // planes per segment
       constexpr int U = kColumnChunk<Real, Geom>;
+      constexpr int NH = HP * LL;
       for (int u = tid; u < HP * K; u += tp) {
-        // u >= 0: unsigned division by the compile-time HP and HL needs no
-        // sign fix-up
-        const unsigned uu = static_cast<unsigned>(u);
-        const int g = static_cast<int>(uu / HP);
-        const int col = static_cast<int>(uu % HP);
-        const int z0 = g * seg;
-        const int hx = static_cast<int>(static_cast<unsigned>(col) % HL);
-        const int y = static_cast<int>(static_cast<unsigned>(col) / HL);
-        const int oyp = (y == LL - 1) ? -(LL - 1) * HL : HL;
-        const int oym = (y == 0) ? (LL - 1) * HL : -HL;
-        const int oxp1 = (hx == HL - 1) ? -(HL - 1) : 1;  // +x offset when x is odd
-        const int oxm0 = (hx == 0) ? (HL - 1) : -1;         // -x offset when x is even
-        // The x parity p of the site flips from plane to plane: sites an even
-        // number of planes after the chunk's first take (pa, oxa), the others
-        // (pb, oxb), so within a chunk the choice is made at compile time.
-        int pa = (y + z0 + c) & 1;
+        // the unit: half index hh of its first site and of that site's -z
+        // neighbour, +-y offsets, and the x parity p of the site: it flips
+        // from plane to plane, so sites an even number of planes after the
+        // chunk's first take (pa, oxa), the others (pb, oxb), and within a
+        // chunk the choice is made at compile time
+        int hh, mzi, oyp, oym, pa, oxa, oxb;
+        if (units != nullptr) {  // from the host's table (column_unit)
+          const int4 d = __ldg(units + u);
+          hh = d.x & 0x7fffffff;
+          pa = static_cast<int>(static_cast<unsigned>(d.x) >> 31) ^ c;
+          mzi = d.y & 0xffff;
+          const int xa = (d.y << 8) >> 24, xb = d.y >> 24;  // signed bytes 2 and 3
+          oxa = c ? xb : xa;
+          oxb = c ? xa : xb;
+          oyp = d.z;
+          oym = d.w;
+        } else {
+          // u >= 0: unsigned division by the compile-time HP and HL needs no
+          // sign fix-up
+          const unsigned uu = static_cast<unsigned>(u);
+          const int g = static_cast<int>(uu / HP);
+          const int col = static_cast<int>(uu % HP);
+          const int z0 = g * seg;
+          const int hx = static_cast<int>(static_cast<unsigned>(col) % HL);
+          const int y = static_cast<int>(static_cast<unsigned>(col) / HL);
+          oyp = (y == LL - 1) ? -(LL - 1) * HL : HL;
+          oym = (y == 0) ? (LL - 1) * HL : -HL;
+          const int oxp1 = (hx == HL - 1) ? -(HL - 1) : 1;  // +x offset when x is odd
+          const int oxm0 = (hx == 0) ? (HL - 1) : -1;         // -x offset when x is even
+          pa = (y + z0 + c) & 1;
+          oxa = pa ? oxp1 : oxm0;
+          oxb = pa ? oxm0 : oxp1;
+          hh = col + HP * z0;
+          mzi = z0 == 0 ? hh + (LL - 1) * HP : hh - HP;
+        }
         int pb = pa ^ 1;
-        int oxa = pa ? oxp1 : oxm0;
-        int oxb = pa ? oxm0 : oxp1;
         const int oxx = oxa ^ oxb;
-        int hh = col + HP * z0;
-        V3<Real> o0 = oth.ld(hh);  // the other colour at the site's half index
-        V3<Real> mz = oth.ld(z0 == 0 ? hh + (LL - 1) * HP : hh - HP);  // -z neighbour
-        for (int zc = z0; zc < z0 + seg; zc += U) {
+        V3<Real> o0 = oth.ld(hh);   // the other colour at the site's half index
+        V3<Real> mz = oth.ld(mzi);  // -z neighbour
+        for (int zc = 0; zc < seg; zc += U) {
 #pragma unroll
           for (int k = 0; k < U; ++k, hh += HP) {
             const int p = (k & 1) ? pb : pa;
             const int nxo = hh + ((k & 1) ? oxb : oxa);
             // chunks start at multiples of U, which divides L: only a chunk's
             // last plane can be plane L - 1, whose +z neighbour wraps
-            const int zn = (k == U - 1 && zc + k == LL - 1) ? hh - (LL - 1) * HP : hh + HP;
+            const int zn = (k == U - 1 && hh + HP >= NH) ? hh + HP - NH : hh + HP;
             const V3<Real> cz = oth.ld(zn);
             const V3<Real> f =
                 add3(add3(add3(add3(add3(o0, oth.ld(nxo)), oth.ld(hh + oyp)), oth.ld(hh + oym)), cz), mz);
@@ -660,24 +653,21 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
   const int init = path_init_mode(P.init_mode, path, sy.n_paths);
   const Real J = static_cast<Real>(sy.J), hf = static_cast<Real>(sy.h);
   const Real bp = A::beta_param(sy.beta);
-  // column segments per column: the divisor K of L, with segments of whole
-  // chunks, that spreads the HP * K units most evenly over the tp threads
-  // (the smallest such K, for the longest segments); 0 = decode every site
-  // (open chains)
+  // column segments per column (column_segments; 0 = decode every site: open
+  // chains), and the host's table of the column-walk units when it was made
+  // for this chunk (the table's K is then that of the same rule)
   int K = 0;
+  const int4* units = nullptr;
   if constexpr (Geom::kColumns) {
     constexpr int LL = 2 * Geom::HL;
     constexpr int U = kColumnChunk<Real, Geom>;
     static_assert(LL % U == 0, "a whole column is a whole number of chunks");
-    double best = -1.0;
-    for (int k = 1; k <= LL; ++k) {
-      if (LL % k || (LL / k) % U) continue;
-      const int units = Geom::HP * k;
-      const double eff = static_cast<double>(units) / (static_cast<double>((units + tp - 1) / tp) * tp);
-      if (eff > best + 1e-9) {
-        best = eff;
-        K = k;
-      }
+    static_assert(Geom::HP * LL < 65536, "unit tables hold half indices in 16 bits");
+    if (P.units != nullptr && sy.unit_off >= 0 && sy.unit_U == U && sy.unit_K > 0) {
+      K = sy.unit_K;
+      units = P.units + sy.unit_off;
+    } else {
+      K = column_segments(LL, U, tp);
     }
   }
   const int64_t j_first = P.s_begin > P.n_therm ? P.s_begin - P.n_therm : 0;
@@ -722,14 +712,14 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
     Partials<Real> part{Real(0), Real(0), Real(0), Real(0)};
     poll_cancel(P, s, tid, &cancel_flag[gidx]);
     if (s < P.n_therm) {
-      half_sweep<Real, Geom, false, false>(geo, 0, pre, P.key, sp, tid, tp, K, J, hf,
+      half_sweep<Real, Geom, false, false>(geo, 0, pre, P.key, sp, tid, tp, K, units, J, hf,
                                            bp, accepted, part);
       group_sync(tp, bar);
       if (cancel_flag[gidx]) {
         canceled = true;
         break;
       }
-      half_sweep<Real, Geom, false, false>(geo, 1, pre, P.key, sp, tid, tp, K, J, hf,
+      half_sweep<Real, Geom, false, false>(geo, 1, pre, P.key, sp, tid, tp, K, units, J, hf,
                                            bp, accepted, part);
       group_sync(tp, bar);
       continue;
@@ -737,7 +727,7 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
     // Measurement sweep j.  Colour-0 sites keep their values during the
     // colour-1 pass, so the colour-1 local fields give every bond once.
     const int64_t j = s - P.n_therm;
-    half_sweep<Real, Geom, true, false>(geo, 0, pre, P.key, sp, tid, tp, K, J, hf, bp,
+    half_sweep<Real, Geom, true, false>(geo, 0, pre, P.key, sp, tid, tp, K, units, J, hf, bp,
                                         accepted, part);
     group_sync(tp, bar);
     if (cancel_flag[gidx]) {
@@ -745,7 +735,7 @@ __device__ __forceinline__ void run_path(const Geom geo, const DevSystem& sy, in
       break;
     }
     meter.maybe_flush(j);
-    half_sweep<Real, Geom, true, true>(geo, 1, pre, P.key, sp, tid, tp, K, J, hf, bp,
+    half_sweep<Real, Geom, true, true>(geo, 1, pre, P.key, sp, tid, tp, K, units, J, hf, bp,
                                        accepted, part);
     meter.record(part);
     group_sync(tp, bar);
