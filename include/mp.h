@@ -403,7 +403,7 @@ int mp_philox(const uint32_t* d_ctr, int64_t n, uint64_t seed, uint32_t* d_out, 
  * queued on `stream` (cudaStream_t; NULL = legacy default stream).  It calls
  * no cudaMalloc, cudaFree or other allocating routine: its scratch (per-path
  * records, work queue, device copies of the tables) is one static __device__
- * array of about 2.9 MB that every GPU loading the library holds until the
+ * array of about 3.4 MB that every GPU loading the library holds until the
  * process exits.  Limits: at most MP_NOALLOC_MAX_PATHS paths in total and
  * MP_NOALLOC_MAX_SYSTEMS systems; larger batches return MP_EINVAL before any
  * GPU work.  The first call on a device looks up the array's device address

@@ -706,8 +706,7 @@ int upload_tables(mp_state* h, const std::vector<WorkItem>& items, bool with_pai
   // table per (L, K, U) shared by every system with those values: the host
   // decodes each unit once instead of every thread at every half-sweep.  U is
   // the chunk of the kernel the plan launches (the mixed-size kernel's for a
-  // batch of uneven sizes); a system left without a table derives its units
-  // on the device.
+  // batch of uneven sizes).
   std::vector<int4> units;
   std::map<std::tuple<int, int, int>, int> unit_at;
   const bool mixed = h->variant == 0;
@@ -719,12 +718,12 @@ int upload_tables(mp_state* h, const std::vector<WorkItem>& items, bool with_pai
     d.unit_U = 0;
     if (h->variant == kRandomSiteKernel || d.lattice != MP_LATTICE_SC || d.mode != kModeShared) continue;
     const int U = column_chunk(real, d.L, mixed);
-    if (d.L % U != 0) continue;
     const int K = column_segments(d.L, U, d.tp);
     const int n_units = d.L * d.L / 2 * K;
     auto it = unit_at.find(std::make_tuple(d.L, K, U));
     if (it == unit_at.end()) {
-      if (static_cast<int64_t>(units.size()) + n_units > h->units_capacity) continue;
+      if (static_cast<int64_t>(units.size()) + n_units > h->units_capacity)
+        return fail(h, MP_ENOMEM, "system %d: no room for its column-walk unit table", k);
       it = unit_at.emplace(std::make_tuple(d.L, K, U), static_cast<int>(units.size())).first;
       for (int u = 0; u < n_units; ++u) units.push_back(column_unit(d.L, K, u));
     }
@@ -1003,9 +1002,8 @@ int mp_create_ex(const mp_config* cfg, mp_handle* out) {
   for (const mp_system& s : h->systems)
     if (s.lattice == MP_LATTICE_SC && s.L <= 26) h->units_capacity += static_cast<int64_t>(s.L) * s.L * s.L / 2;
   h->d_units = h->units_capacity > 0 ? static_cast<int4*>(dev_alloc(h, sizeof(int4) * h->units_capacity)) : nullptr;
-  if (h->units_capacity > 0 && !h->d_units) h->units_capacity = 0;  // the device derives the units
   if (!h->d_sys || !h->d_items || !h->d_queue || !h->d_rec || !h->d_est || !h->d_spin_offset ||
-      !h->d_thr)
+      !h->d_thr || (h->units_capacity > 0 && !h->d_units))
     return bail(fail(h, MP_ENOMEM, "device allocation failed"));
   h->d_error = static_cast<int*>(dev_alloc(h, 256));
   if (!h->d_error) return bail(fail(h, MP_ENOMEM, "device allocation failed"));

@@ -9,9 +9,9 @@
 //
 // This file keeps everything else a run needs -- the per-path records that
 // pass from the sweep kernel to the reduction kernel, the work-queue counter,
-// and the device copies of the system and work-item tables -- in one
-// file-scope __device__ array of fixed size.  Every GPU that loads the
-// library holds that array (about 2.9 MB) until the process exits.
+// and the device copies of the system, work-item and column-walk unit tables
+// -- in one file-scope __device__ array of fixed size.  Every GPU that loads
+// the library holds that array (about 3.4 MB) until the process exits.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,10 +29,20 @@ using mpk::WorkItem;
 
 constexpr int kMaxDevices = 64;
 
+// Column-walk units: one table per lattice size of a call (the threads per
+// path and so the segment count depend on L alone here), at most L^3/2
+// entries for each even L up to the largest size shared memory holds.
+constexpr int kMaxUnits = [] {
+  int n = 0;
+  for (int L = 2; L <= 26; L += 2) n += L * L * L / 2;
+  return n;
+}();
+
 struct NoallocScratch {
   double records[static_cast<size_t>(MP_NOALLOC_MAX_PATHS) * MP_NREC];
   WorkItem items[MP_NOALLOC_MAX_PATHS];
   DevSystem systems[MP_NOALLOC_MAX_SYSTEMS];
+  int4 units[kMaxUnits];
   int queue[64];  // queue[0]: the work counter, queue[1]: the kernels' error word
 };
 
@@ -44,6 +54,7 @@ std::mutex g_mu;                                  // serialises host-side set-up
 NoallocScratch* g_addr[kMaxDevices] = {nullptr};  // device address, per device
 WorkItem g_items[MP_NOALLOC_MAX_PATHS];           // host staging of the tables
 DevSystem g_systems[MP_NOALLOC_MAX_SYSTEMS];
+int4 g_units[kMaxUnits];
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
@@ -102,7 +113,9 @@ extern "C" int mp_run_noalloc(const mp_system* systems, int n_systems, int preci
     return MP_ECUDA;
   }
   const int real = precision == MP_FP64 ? 8 : 4;
-  int cta = 32, smem = 0, n_items = 0;
+  int cta = 32, smem = 0, n_items = 0, n_units = 0;
+  int unit_of_L[27];  // first unit-table entry of each size, -1 = none yet
+  std::fill(unit_of_L, unit_of_L + 27, -1);
   int64_t rec = 0, max_paths = 0;
   for (int k = 0; k < n_systems; ++k) {
     const mp_system& s = systems[k];
@@ -128,7 +141,20 @@ extern "C" int mp_run_noalloc(const mp_system* systems, int n_systems, int preci
     ds.rec_offset = rec;
     ds.n_paths = s.n_paths;
     ds.path_begin = s.path_begin;
-    ds.unit_off = -1;  // no unit tables: the column walk derives its units on the device
+    ds.unit_off = -1;
+    if (s.lattice == MP_LATTICE_SC) {  // the column walk's units (column_unit)
+      const int U = mpk::column_chunk(real, s.L, variant == 0);
+      const int K = mpk::column_segments(s.L, U, tp);
+      const int cnt = s.L * s.L / 2 * K;
+      if (s.L > 26 || (unit_of_L[s.L] < 0 && n_units + cnt > kMaxUnits)) return MP_EINVAL;
+      if (unit_of_L[s.L] < 0) {
+        unit_of_L[s.L] = n_units;
+        for (int u = 0; u < cnt; ++u) g_units[n_units++] = mpk::column_unit(s.L, K, u);
+      }
+      ds.unit_off = unit_of_L[s.L];
+      ds.unit_K = K;
+      ds.unit_U = U;
+    }
     for (int64_t p = 0; p < s.n_paths; ++p) g_items[n_items++] = WorkItem{k, 1, p};
     rec += s.n_paths;
     cta = std::max(cta, tp);
@@ -146,6 +172,8 @@ extern "C" int mp_run_noalloc(const mp_system* systems, int n_systems, int preci
                       st) != cudaSuccess ||
       cudaMemcpyAsync(d->items, g_items, sizeof(WorkItem) * n_items, cudaMemcpyHostToDevice, st) !=
           cudaSuccess ||
+      (n_units > 0 &&
+       cudaMemcpyAsync(d->units, g_units, sizeof(int4) * n_units, cudaMemcpyHostToDevice, st) != cudaSuccess) ||
       cudaMemsetAsync(d->queue, 0, 2 * sizeof(int), st) != cudaSuccess) {
     cudaGetLastError();
     return MP_ECUDA;
@@ -165,6 +193,7 @@ extern "C" int mp_run_noalloc(const mp_system* systems, int n_systems, int preci
   p.s_end = n_therm + n_meas;
   p.key = mpk::philox_round_keys(seed);
   p.error = d->queue + 1;  // where a kernel would report a path that stopped early
+  p.units = d->units;
   mpk::ReduceParams r{};
   r.systems = d->systems;
   r.records = d->records;
