@@ -67,7 +67,8 @@ __device__ __forceinline__ void ising_half_sweep(int Lrt, uint32_t sweep, uint32
   for (int t = tid; t < strips; t += tp) {
     const Philox4 r = philox4x32_10(static_cast<uint32_t>(t), pre, key);
     const uint32_t w[4] = {r.x, r.y, r.z, r.w};
-    const int j = t / HL;
+    // t >= 0: unsigned division by HL (a compile-time constant for kL > 0)
+    const int j = static_cast<int>(static_cast<unsigned>(t) / static_cast<unsigned>(HL));
     const int hx = t - j * HL;
     const int oxp1 = (hx == HL - 1) ? -(HL - 1) : 1;  // +x offset when x is odd
     const int oxm0 = (hx == 0) ? (HL - 1) : -1;         // -x offset when x is even
