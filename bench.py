@@ -120,14 +120,14 @@ BYTES_PER_ATTEMPT_FP32 = 24
 # with this hash (sha256 over csrc/, first 16 hex digits); any change of the
 # sources voids it and the roofline reports traffic null.  Each is the timed
 # launch of the workload's bench command, captured at full size (one ncu pass):
-# sc16 reads 1.16 MB (tables; the lattices stay in shared memory), batched
-# 0.70 MB (every size, L = 32 included, stays in shared memory), large moves
-# 28.94 TB against 28.99 TB of algorithmic bytes, ising 0.34 MB.
+# sc16 reads 0.72 MB (tables; the lattices stay in shared memory), batched
+# 0.73 MB (every size, L = 32 included, stays in shared memory), large moves
+# 28.95 TB against 28.99 TB of algorithmic bytes, ising 0.48 MB.
 TRAFFIC = {
-    "sc16": {"sources": "1c248258599d7be3", "bytes": 1.160960e6},
-    "large": {"sources": "1c248258599d7be3", "bytes": 14.437677e12 + 14.502217e12},
-    "batched": {"sources": "1c248258599d7be3", "bytes": 0.703232e6},
-    "ising": {"sources": "1c248258599d7be3", "bytes": 0.336896e6 + 256},
+    "sc16": {"sources": "3edd2e2a4ef88d1e", "bytes": 0.720128e6},
+    "large": {"sources": "3edd2e2a4ef88d1e", "bytes": 14.453252e12 + 14.496706e12},
+    "batched": {"sources": "3edd2e2a4ef88d1e", "bytes": 0.733696e6},
+    "ising": {"sources": "3edd2e2a4ef88d1e", "bytes": 0.483840e6},
 }
 
 
