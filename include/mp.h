@@ -106,6 +106,10 @@ extern "C" {
                                      never issue their first bulk copy, so the
                                      kernel's bounded wait runs out (about 2 s)
                                      and mp_estimates returns MP_ETIMEOUT */
+#define MP_FLAG_DEVICE_UNITS 0x200u /* for tests: make no column-walk unit tables;
+                                       the shared-memory walk derives each unit
+                                       on the device instead (the same units and
+                                       results, more instructions per unit) */
 
 /* ------------------------------------------------------------- records ---
  * Per-path record: MP_NREC doubles per path.  Fields 0..12 are means over the

@@ -27,6 +27,7 @@ FP32, FP64 = 0, 1
 INIT_SPHERE, INIT_ANGLES, INIT_ORDERED = 0, 1, 2
 FLAG_GRAPH, FLAG_KEEP_SPINS, FLAG_STREAM, FLAG_AUTOTUNE, FLAG_TWO_START, FLAG_RANDOM_SITE = 1, 2, 4, 8, 16, 32
 FLAG_TEST_STALL = 0x100
+FLAG_DEVICE_UNITS = 0x200
 
 MP_OK, MP_EINVAL, MP_ENOMEM, MP_ECUDA, MP_ESTATE, MP_ECANCELED, MP_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 

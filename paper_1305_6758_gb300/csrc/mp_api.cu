@@ -716,7 +716,9 @@ int upload_tables(mp_state* h, const std::vector<WorkItem>& items, bool with_pai
     d.unit_off = -1;
     d.unit_K = 0;
     d.unit_U = 0;
-    if (h->variant == kRandomSiteKernel || d.lattice != MP_LATTICE_SC || d.mode != kModeShared) continue;
+    if ((h->flags & MP_FLAG_DEVICE_UNITS) || h->variant == kRandomSiteKernel || d.lattice != MP_LATTICE_SC ||
+        d.mode != kModeShared)
+      continue;
     const int U = column_chunk(real, d.L, mixed);
     const int K = column_segments(d.L, U, d.tp);
     const int n_units = d.L * d.L / 2 * K;
@@ -853,7 +855,7 @@ std::map<std::string, std::vector<int>> g_tune_memo;
 
 std::string tune_key(const mp_state* h, const mp_config* cfg) {
   std::string k = std::to_string(h->device) + "/" + std::to_string(h->precision) + "/" +
-                  std::to_string(h->flags & (MP_FLAG_STREAM | MP_FLAG_TWO_START)) + "/" +
+                  std::to_string(h->flags & (MP_FLAG_STREAM | MP_FLAG_TWO_START | MP_FLAG_DEVICE_UNITS)) + "/" +
                   std::to_string(h->init_mode) + "/" + std::to_string(cfg->cta_threads);
   for (const mp_system& s : h->systems)
     k += "/" + std::to_string(s.lattice) + ":" + std::to_string(s.L) + ":" + std::to_string(s.n_paths);
