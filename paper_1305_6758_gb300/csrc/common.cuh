@@ -120,13 +120,13 @@ struct SweepParams {
 // 16 (a whole column at L = 8), 6 for 12, 18 and 24, 4 for 20, 7 for 14, 3 for
 // 6, 2 for 10, 22 and 26, 1 for 2 and 4 (whose columns are too short to split
 // into chunks).  The mixed-size kernel holds every size's walk in one register
-// allocation and takes 3 for 12 and 18 and 2 for 14, which keep it within 128
-// registers without spills, and 6 for 24.  FP64 kernels (64 registers per
-// thread) take one site at a time.  Measured on the benchmark layouts: chunks
-// of 2 lose 6% against 4, 8 gains 1% over 4 at L = 16, 16 spills; whole chunks
-// of 6 gain 6-8% over a runtime unroll of 4 at L = 12, 18, 24; in the batch of
-// uneven sizes, 8 at L = 8 and 6 at L = 24 gain 1.3% together, while 6 at
-// L = 12 loses 1%.
+// allocation and takes 3 for 12 and 18, 2 for 14 and 6 for 24.  FP64 kernels
+// (64 registers per thread) take one site at a time.  Measured on the
+// benchmark layouts: chunks of 2 lose 6% against 4; 8 gains 1% over 4 at
+// L = 16, and 16 (a whole column, spill-free) loses 4% against 8; whole
+// chunks of 6 gain 6-8% over a runtime unroll of 4 at L = 12, 18, 24; in the
+// batch of uneven sizes, 8 at L = 8 and 6 at L = 24 gain 1.3% together, while
+// 6 or 4 at L = 12 lose 0.2-1%.
 __host__ __device__ constexpr int column_chunk_fp32(int L, bool mixed) {
   return (L == 16 || L == 8)       ? 8
          : (L % 6 == 0 && L >= 12) ? ((mixed && L < 24) ? 3 : 6)
