@@ -120,14 +120,14 @@ BYTES_PER_ATTEMPT_FP32 = 24
 # with this hash (sha256 over csrc/, first 16 hex digits); any change of the
 # sources voids it and the roofline reports traffic null.  Each is the timed
 # launch of the workload's bench command, captured at full size (one ncu pass):
-# sc16 reads 0.72 MB (tables; the lattices stay in shared memory), batched
+# sc16 reads 0.86 MB (tables; the lattices stay in shared memory), batched
 # 0.73 MB (every size, L = 32 included, stays in shared memory), large moves
-# 28.95 TB against 28.99 TB of algorithmic bytes, ising 0.48 MB.
+# 28.95 TB against 28.99 TB of algorithmic bytes, ising 0.36 MB.
 TRAFFIC = {
-    "sc16": {"sources": "3edd2e2a4ef88d1e", "bytes": 0.720128e6},
-    "large": {"sources": "3edd2e2a4ef88d1e", "bytes": 14.453252e12 + 14.496706e12},
-    "batched": {"sources": "3edd2e2a4ef88d1e", "bytes": 0.733696e6},
-    "ising": {"sources": "3edd2e2a4ef88d1e", "bytes": 0.483840e6},
+    "sc16": {"sources": "95a18dbaf2d46fb2", "bytes": 0.860672e6},
+    "large": {"sources": "95a18dbaf2d46fb2", "bytes": 14.458694e12 + 14.496286e12},
+    "batched": {"sources": "95a18dbaf2d46fb2", "bytes": 0.734208e6},
+    "ising": {"sources": "95a18dbaf2d46fb2", "bytes": 0.356608e6},
 }
 
 
