@@ -522,7 +522,7 @@ def main():
     autotuned = [sim.system_plan(k) for k in (range(n_sys) if n_sys <= 8 else sorted({0, n_sys // 2, n_sys - 1}))]
     sim.close()
 
-    # end to end through the public API: create (system and work tables H2D),
+    # end to end through the public API: create (the plan's tables H2D),
     # run, read every system's estimates (D2H), destroy -- all inside the clock;
     # the library remembers the autotuner's choice for a batch of this shape,
     # so these creates do not time layouts again
